@@ -1,0 +1,100 @@
+"""Pins of the oracle's ANLS sweep (Alg. "anls", Sec. 2, Y-update first).
+
+Independent evidence: every column/row of a sweep equals an exhaustive
+passive-set search on products formed here with numpy; the objective never
+increases (each half step is an exact minimisation, Sec. 2); noiseless data
+started near the truth are recovered; permuting the time columns permutes Y
+and leaves X unchanged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._brute import brute_nnls
+
+
+def test_sweep_matches_brute_force_per_column_and_row():
+    M, _, _ = synth.pdf_like(24, 11, 3, noise=1e-2, seed=3)
+    X, Y = synth.init_factors(24, 11, 3, seed=3)
+    Xn, Yn, xm, ym, st = oracle.sweep(M, X, Y)
+    assert st == oracle.OK
+    G = X.T @ X
+    for j in range(M.shape[1]):
+        yb = brute_nnls(G, X.T @ M[:, j])
+        np.testing.assert_allclose(Yn[:, j], yb, rtol=1e-9, atol=1e-12)
+        assert ym[j] == sum(1 << a for a in range(3) if yb[a] > 0)
+    H = Yn @ Yn.T
+    P = M @ Yn.T
+    for i in range(M.shape[0]):
+        xb = brute_nnls(H, P[i])
+        np.testing.assert_allclose(Xn[i], xb, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_objective_non_increasing(seed):
+    M, _, _ = synth.pdf_like(80, 30, 4, noise=1e-3, seed=seed)
+    X, Y = synth.init_factors(80, 30, 4, seed=seed)
+    f_prev = oracle.objective(M, X, Y)
+    for _ in range(25):
+        X, Y, _, _, st = oracle.sweep(M, X, Y)
+        assert st == oracle.OK
+        f = oracle.objective(M, X, Y)
+        assert f <= f_prev * (1 + 1e-12) + 1e-300
+        f_prev = f
+
+
+def test_noiseless_recovery_from_near_truth():
+    n, m, k = 60, 25, 3
+    _, X0, Y0 = synth.pdf_like(n, m, k, noise=0.0, seed=5)
+    M = X0 @ Y0
+    rs = np.random.default_rng(0)
+    X = X0 * (1 + 0.05 * rs.uniform(-1, 1, size=X0.shape)) + 1e-3
+    Y = Y0 * (1 + 0.05 * rs.uniform(-1, 1, size=Y0.shape)) + 1e-3
+    X, Y, _, _, sw, tr, st = oracle.anls(M, X, Y, max_sweeps=400, want_trace=True)
+    assert st == oracle.OK
+    assert tr[-1, 0] / (0.5 * np.sum(M ** 2)) < 1e-12
+    np.testing.assert_allclose(X @ Y, M, rtol=0, atol=1e-5 * np.abs(M).max())
+
+
+def test_column_permutation_equivariance():
+    M, _, _ = synth.pdf_like(40, 15, 3, noise=1e-3, seed=8)
+    X, Y = synth.init_factors(40, 15, 3, seed=8)
+    perm = np.random.default_rng(1).permutation(15)
+    Xa, Ya = X, Y
+    Xb, Yb = X, Y[:, perm]
+    Xa, Ya, _, _, _ = oracle.sweep(M, Xa, Ya)
+    Xb, Yb, _, _, _ = oracle.sweep(M[:, perm], Xb, Yb)
+    # equal up to the reordered sums over j; the X rows are solved with
+    # H = Y Y^T, so their rounding is amplified by up to cond(H)
+    eps = np.finfo(float).eps
+    np.testing.assert_allclose(Yb, Ya[:, perm], rtol=1e-12, atol=1e-15)
+    tol = 100 * np.linalg.cond(Ya @ Ya.T) * eps
+    np.testing.assert_allclose(Xb, Xa, rtol=tol, atol=tol * np.abs(Xa).max())
+
+
+def test_first_sweep_from_any_start_is_independent_of_initial_y():
+    """Y-first ordering: sweep 1's Y depends on X only (the NNLS is solved
+    exactly, so the old Y does not matter)."""
+    M, _, _ = synth.pdf_like(30, 12, 3, noise=1e-3, seed=2)
+    X, Y = synth.init_factors(30, 12, 3, seed=2)
+    a = oracle.sweep(M, X, Y)
+    b = oracle.sweep(M, X, 5.0 * Y + 1.0)
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[0], b[0])
+
+
+def test_step_tolerance_stop():
+    M, _, _ = synth.pdf_like(50, 20, 3, noise=1e-3, seed=4)
+    X, Y = synth.init_factors(50, 20, 3, seed=4)
+    _, _, _, _, sw, tr, st = oracle.anls(M, X, Y, max_sweeps=5000, stol=1e-4, want_trace=True)
+    assert st == oracle.OK and sw < 5000
+    assert tr[sw - 1, 3] <= 1e-4 and np.all(tr[: sw - 1, 3] > 1e-4)
+
+
+def test_kkt_target_stop_and_convergence():
+    M, _, _ = synth.pdf_like(60, 20, 3, noise=1e-3, seed=6)
+    X, Y = synth.init_factors(60, 20, 3, seed=6)
+    _, _, _, _, sw, tr, st = oracle.anls(M, X, Y, max_sweeps=20000, kkt_target=1e-6, want_trace=True)
+    assert st == oracle.OK and sw < 20000
+    assert tr[sw, 2] <= 1e-6 and np.all(tr[:sw, 2] > 1e-6)
