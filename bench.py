@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the stage-1 ANLS sweep on GB300.
+
+Workload: the FP64-vs-FP32-pass configuration -- synthetic PDF-like data,
+n = 3000 rows, m = 2000 time columns, k = 4, 1e-3 relative noise.  A step is
+one full ANLS sweep (Y-update with the fused M pass, X-update, objective and
+KKT terms) of the mixed-precision form (FP32 M, FP32 contraction, FP64 NNLS /
+Grams / KKT).  L2 is flushed (256 MB write) before every timed step, so every
+step reads M from HBM.
+
+Also reported: the plain FP64 form and the FP64-accumulated refinement pass
+(sweeps/s), time to relative KKT 1e-8 for the mixed and the FP64 form,
+achieved HBM bandwidth of the M pass against the measured peak, an end-to-end
+figure through the C ABI with host buffers, and the CPU oracle timed on the
+host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own problem (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel. KKT 1e-8 (s); ANLS sweeps/s; HBM GB/s — mixed vs FP64 on 1 GB300"
+N_ROWS, M_COLS, RANK_K, NOISE = 3000, 2000, 4, 1e-3
+FLUSH_BYTES = 256 << 20
+PRECOND = 400     # sweeps from the U[0,1] start before timing: steady-state sweeps are timed
+WORKLOAD = "PDF-like streaming NMF n=3000 m=2000 k=4 (1e-3 rel. noise), one ANLS sweep of the mixed form"
+YPASS_SOURCES = ["paper_2101_08431_gb300/csrc/nmf_sweep.cuh", "paper_2101_08431_gb300/csrc/nmf_nnls.cuh",
+                 "paper_2101_08431_gb300/csrc/nmf_common.cuh"]
+TRAFFIC_FILE = "profiles/ypass_f32_n3000_m2000_k4.md"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in YPASS_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per M-pass launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, TRAFFIC_FILE)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    mb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mb or mh.group(1) != kernel_hash():
+        return None
+    return float(mb.group(1))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_data(seed):
+    import synth
+    M, _, _ = synth.pdf_like(N_ROWS, M_COLS, RANK_K, noise=NOISE, relative=True, seed=seed)
+    X0, Y0 = synth.init_factors(N_ROWS, M_COLS, RANK_K, seed=seed)
+    return np.asfortranarray(M.astype(np.float32)), np.asfortranarray(M), X0, Y0
+
+
+def cpu_sweep_rate(M64, X0, Y0, budget_s=12.0, min_sweeps=3):
+    """The oracle as it stands, single-threaded, on a bounded sample: whole
+    sweeps of the same problem until budget_s has elapsed."""
+    import oracle
+    oracle.build()
+    X, Y = X0, Y0
+    t0 = time.perf_counter()
+    n = 0
+    while n < min_sweeps or time.perf_counter() - t0 < budget_s:
+        X, Y, _, _, st = oracle.sweep(M64, X, Y)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    _, M64, X0, Y0 = make_data(0)
+    import oracle
+    oracle.build()
+    X, Y = X0, Y0
+    for _ in range(args.warmup):
+        X, Y, _, _, _ = oracle.sweep(M64, X, Y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        X, Y, _, _, _ = oracle.sweep(M64, X, Y)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_ROWS, "m": M_COLS, "k": RANK_K},
+            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full oracle sweeps of the workload" % args.steps},
+            "e2e": {"value": v, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2101_08431_gb300 import NMF_PREC_FP64, NMF_PREC_MIXED, StreamingNMF, build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)          # a real stream handle (the default stream is 0)
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    M32, M64, X0, Y0 = make_data(rank)
+    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_sweeps(h, steps, warmup, precond=0):
+        if precond:
+            h.sweep(precond, want_stats=False)
+        for _ in range(warmup):
+            flush()
+            h.sweep(1, want_stats=False)
+        h.set_timing(True)
+        l0 = h.launches
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for e0, e1 in ev:
+            flush()
+            e0.record(stream)
+            h.sweep(1, want_stats=False)
+            e1.record(stream)
+        barrier()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        launches = h.launches - l0
+        tm = h.get_timing()
+        h.set_timing(False)
+        return ms, launches, tm
+
+    def time_to_target(h, X, Y):
+        h.set_factors(X, Y)
+        h.set_pass_mode(-1)
+        flush()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        st = h.sweep(0, allow_notconv=True)
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        return {"seconds": e0.elapsed_time(e1) / 1e3, "wall_s": wall, "sweeps": st["sweeps"],
+                "fp64_sweeps": st["fp64_sweeps"], "kkt_rel": st["kkt_rel"], "converged": bool(st["converged"]),
+                "f": st["f"]}
+
+    out = {}
+    # ---- mixed form, FP32 pass (the headline step)
+    hm = StreamingNMF(N_ROWS, RANK_K, M_COLS, prec=NMF_PREC_MIXED, kkt_target=1e-8, max_sweeps=60000,
+                      stream=sptr)
+    hm.append_columns(M32)
+    hm.set_factors(X0, Y0)
+    hm.set_pass_mode(0)
+    with ClockSampler(local) as clk:
+        ms, launches, tm = timed_sweeps(hm, args.steps, args.warmup, PRECOND)
+    ms = max_over_ranks(ms)
+    out["value"] = world * args.steps / (ms / 1e3)
+    out["ms_per_step"] = ms / args.steps
+    out["gpu_launches"] = launches
+    y_avg_ms = tm["ypass_ms"] / max(tm["ypass_launches"], 1)
+    x_avg_ms = tm["xpass_ms"] / max(tm["xpass_launches"], 1)
+    alg_bytes = N_ROWS * M_COLS * 4 + 2 * M_COLS * RANK_K * 8 + N_ROWS * RANK_K * 4
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (y_avg_ms / 1e3) / 1e9
+    traffic = measured_traffic()
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                       "kernel": "ypass (fused M pass, FP32)", "alg_bytes_per_launch": alg_bytes,
+                       "avg_launch_ms": y_avg_ms, "xpass_avg_ms": x_avg_ms}
+    out["clocks"] = clk.summary()
+    # ---- mixed form, FP64-accumulated refinement pass
+    hm.set_pass_mode(1)
+    ms_r, _, tm_r = timed_sweeps(hm, max(10, args.steps // 4), 3)
+    yr = tm_r["ypass_ms"] / max(tm_r["ypass_launches"], 1)
+    out["refine_pass"] = {"sweeps_per_s": max(10, args.steps // 4) / (max_over_ranks(ms_r) / 1e3) * world,
+                          "ypass_avg_ms": yr, "ypass_gbs": alg_bytes / (yr / 1e3) / 1e9}
+    # ---- plain FP64 form
+    hf = StreamingNMF(N_ROWS, RANK_K, M_COLS, prec=NMF_PREC_FP64, kkt_target=1e-8, max_sweeps=60000,
+                      stream=sptr)
+    hf.append_columns(M64)
+    hf.set_factors(X0, Y0)
+    nf = max(10, args.steps // 4)
+    ms_f, _, tm_f = timed_sweeps(hf, nf, 3, PRECOND)
+    yf = tm_f["ypass_ms"] / max(tm_f["ypass_launches"], 1)
+    fbytes = N_ROWS * M_COLS * 8 + 2 * M_COLS * RANK_K * 8 + N_ROWS * RANK_K * 8
+    out["fp64_form"] = {"sweeps_per_s": world * nf / (max_over_ranks(ms_f) / 1e3), "ypass_avg_ms": yf,
+                        "ypass_gbs": fbytes / (yf / 1e3) / 1e9,
+                        "ypass_fp64_tflops": 4.0 * N_ROWS * M_COLS * RANK_K / (yf / 1e3) / 1e12}
+    # ---- time to relative KKT 1e-8 from the same start
+    if not args.skip_ttk:
+        out["time_to_kkt"] = {"mixed": time_to_target(hm, X0, Y0), "fp64": time_to_target(hf, X0, Y0)}
+    # ---- end to end through the C ABI with host buffers
+    pinned = torch.empty((M_COLS, N_ROWS), dtype=torch.float32, pin_memory=True)
+    pinned.numpy()[:] = M32.T
+    hm.set_factors(X0, Y0)
+    hm.set_pass_mode(0)
+    pin_view = pinned.t()            # n x m, column-major view for the ABI
+    ne = max(10, args.steps // 4)
+    for _ in range(2):
+        hm.append_columns(pin_view)
+        hm.sweep(1)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ne):
+        hm.append_columns(pin_view)
+        st = hm.sweep(1)
+    e1.record(stream)
+    barrier()
+    ms_e = max_over_ranks(e0.elapsed_time(e1))
+    out["e2e"] = {"value": world * ne / (ms_e / 1e3), "unit": "sweeps/s",
+                  "h2d_bytes_per_step": N_ROWS * M_COLS * 4, "d2h_bytes_per_step": 8 * 1024 + 4,
+                  "step": "append all m columns from pinned host memory, one sweep, read the statistics"}
+    hm.close()
+    hf.close()
+    # ---- CPU baseline (rank 0 at N = 1 only)
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        v, nsw, dt = cpu_sweep_rate(M64, X0, Y0)
+        out["cpu_baseline"] = {"value": v, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+                               "sample": "%d full sweeps of the workload in %.1f s, single thread" % (nsw, dt)}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": out["value"], "unit": "sweeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_ROWS, "m": M_COLS, "k": RANK_K,
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "state": "steady state: timed sweeps follow %d sweeps from the U[0,1] start" % PRECOND,
+                       "parallelism": "independent problem per GPU" if world > 1 else "single GPU"}}
+    for key in ("roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks", "refine_pass", "fp64_form",
+                "time_to_kkt"):
+        if key in out:
+            line[key] = out[key]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ncu_case(args):
+    """A short, fixed launch sequence for ncu captures: priming, PRECOND_NCU
+    sweeps of the chosen pass, then 3 more (capture them with -s/-c)."""
+    import torch
+    from paper_2101_08431_gb300 import NMF_PREC_FP64, NMF_PREC_MIXED, StreamingNMF, build
+    build.build()
+    M32, M64, X0, Y0 = make_data(0)
+    fp64 = args.ncu_case == "f64"
+    h = StreamingNMF(N_ROWS, RANK_K, M_COLS, prec=NMF_PREC_FP64 if fp64 else NMF_PREC_MIXED, kkt_target=0.0)
+    h.append_columns(M64 if fp64 else M32)
+    h.set_factors(X0, Y0)
+    if not fp64:
+        h.set_pass_mode(1 if args.ncu_case == "ref" else 0)
+    h.sweep(args.ncu_precond + 3, want_stats=False)
+    torch.cuda.synchronize()
+    h.close()
+    print("ncu case %s: 1 priming pair + %d sweeps" % (args.ncu_case, args.ncu_precond + 3))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-ttk", action="store_true")
+    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64"], default=None,
+                    help="run only a short launch sequence for an ncu capture")
+    ap.add_argument("--ncu-precond", type=int, default=200)
+    args = ap.parse_args()
+    if args.ncu_case:
+        return run_ncu_case(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * nmf.h -- C ABI of the GB300 (sm_103a) streaming-NMF library.
+ *
+ * The library implements the hot path of the two-stage method of Gu, Du and
+ * Billinge, "A fast two-stage algorithm for non-negative matrix factorization
+ * in streaming data" (arXiv 2101.08431): the stage-1 ANLS sweep for
+ *
+ *     min 1/2 ||X Y - M||_F^2   s.t.  X >= 0, Y >= 0            (eq. "prob", Sec. 1)
+ *
+ * with M (n x m) whose columns are time instants that arrive progressively
+ * (Sec. 1).  Each sweep solves every column of Y and then every row of X as an
+ * independent nonnegative least-squares problem (eq. "qp", Sec. 2) with the
+ * Lawson-Hanson active-set method warm-started from the previous solution
+ * and its passive set (Sec. 2).
+ *
+ * Conventions for every entry point:
+ *   - Layouts: M and appended columns are column-major (element (i, j) at
+ *     i + ld*j); X is n x k row-major (X[i*k + a], the vector x = vec(X^T) of
+ *     Sec. 3.1); Y is k x m column-major (Y[a + k*j], y = vec(Y)); passive-set
+ *     masks are one uint32 per column of Y / row of X, bit a set when
+ *     component a is positive.
+ *   - Pointers are borrowed for the duration of the call only; data are
+ *     copied into library-owned device memory.  `on_device` = 1 means the
+ *     pointer is CUDA device memory, 0 means host memory (pinned host memory
+ *     gives asynchronous copies).  Output buffers belong to the caller.
+ *   - Streams: all device work of a handle is ordered on the stream given in
+ *     its nmf_config (NULL: the library creates one).  Calls that return data
+ *     to the host (nmf_get_factors, nmf_objective_kkt, nmf_sweep when it
+ *     fills stats) synchronise that stream.
+ *   - Errors: every call returns an nmf_status; nothing aborts or throws
+ *     across the ABI.  After NMF_ECUDA or NMF_ETIMEOUT the handle is poisoned
+ *     (every later call returns the same status) until nmf_destroy.
+ *     nmf_last_error gives a one-line explanation of the last failure.
+ *   - Threading: a handle is used by one thread at a time; distinct handles
+ *     are independent.
+ */
+#ifndef NMF_GB300_H
+#define NMF_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nmf_handle nmf_handle;
+
+typedef enum {
+    NMF_OK = 0,
+    NMF_EINVAL = 1,      /* bad argument or unsupported size                 */
+    NMF_ENOMEM = 2,      /* device or host allocation failed                 */
+    NMF_ECUDA = 3,       /* CUDA runtime error (handle poisoned)             */
+    NMF_ENOTCONV = 4,    /* iteration cap reached before the stopping test   */
+    NMF_ETIMEOUT = 5,    /* a bounded device wait gave up (handle poisoned)  */
+    NMF_ECAPACITY = 6,   /* request exceeds the handle's capacity            */
+    NMF_ENUMERIC = 7,    /* NaN or Inf in the data or the iterates           */
+    NMF_ESTATE = 8       /* call out of order (e.g. sweep before factors)    */
+} nmf_status;
+
+typedef enum {
+    NMF_PREC_FP64 = 0,   /* M stored and contracted in FP64                  */
+    NMF_PREC_MIXED = 1   /* M stored FP32; FP32 passes, then FP64-accumulated
+                            refinement passes; NNLS, Grams and KKT in FP64   */
+} nmf_precision;
+
+enum { NMF_DTYPE_F64 = 0, NMF_DTYPE_F32 = 1 };
+enum { NMF_WARM_COLD = 0, NMF_WARM_PREV = 1 };
+
+typedef struct {
+    int64_t n;               /* rows of M (distance grid)                     */
+    int64_t m_capacity;      /* resident time columns (ring buffer capacity)  */
+    int32_t k;               /* rank, 1..8 or 16                              */
+    int32_t prec;            /* nmf_precision                                 */
+    double stol;             /* eps_STOL of the Sec. 4 relative step test;
+                                <= 0 disables                                 */
+    double kkt_target;       /* stop when the relative KKT error <= target;
+                                <= 0 disables                                 */
+    double mixed_switch;     /* MIXED: move to FP64-accumulated passes once the
+                                relative KKT error <= this (or stalls)       */
+    int32_t max_sweeps;      /* cap for nmf_sweep(h, 0, ...)                  */
+    int32_t warm_start;      /* NMF_WARM_COLD or NMF_WARM_PREV                */
+    void *cuda_stream;       /* cudaStream_t, or NULL                         */
+} nmf_config;
+
+typedef struct {
+    int32_t sweeps;          /* sweeps run by this call                        */
+    int32_t iter;            /* index of the current iterate                   */
+    int32_t converged;       /* 1 rel-KKT target met, 2 step test met, 0 not   */
+    int32_t fp64_sweeps;     /* sweeps of this call whose M pass ran in FP64   */
+    double f;                /* 1/2 ||XY - M||^2 of the last measured iterate  */
+    double kkt_abs;          /* E(x, y, r, s; 0) with r = max(graX,0),
+                                s = max(graY,0) (Sec. 5.1), 2-norms            */
+    double kkt_rel;          /* kkt_abs terms scaled (see nmf_objective_kkt)   */
+    double step_rel;         /* ||Δ(x,y)|| / (1 + ||(x,y)||) (Sec. 4)          */
+    int64_t changed_cols;    /* columns whose passive set changed (last sweep) */
+    int64_t changed_rows;    /* rows whose passive set changed (last sweep)    */
+    int64_t nnls_notconv;    /* NNLS solves that hit their iteration cap       */
+    int32_t measured_iter;   /* iterate the f / KKT figures belong to          */
+    int32_t pad;
+} nmf_stats;
+
+/* Defaults: stol 0, kkt_target 1e-8, mixed_switch 1e-6, max_sweeps 100000,
+ * warm_start NMF_WARM_PREV, prec NMF_PREC_MIXED. */
+void nmf_config_init(nmf_config *cfg);
+
+/* Create a handle for one problem of n rows, rank k and up to m_capacity
+ * resident columns (Sec. 1's streaming setting).  Allocates all device
+ * memory up front; no allocation happens in later calls except
+ * nmf_append_columns' staging of host data.  Errors: NMF_EINVAL for n < 1,
+ * k outside 1..8 and 16, m_capacity < 1 or n beyond the kernels' row limit
+ * (16384 rows FP32, 8192 FP64); NMF_ENOMEM; NMF_ECUDA. */
+nmf_status nmf_create(const nmf_config *cfg, nmf_handle **out);
+
+/* Free every resource of the handle (NULL is accepted). */
+nmf_status nmf_destroy(nmf_handle *h);
+
+/* Append ncols time columns (n x ncols, column-major, leading dimension ld,
+ * dtype NMF_DTYPE_F32/F64) to the resident window (Sec. 1: data arrive by
+ * columns).  When the window would exceed m_capacity the oldest columns are
+ * evicted.  A new column's y is seeded with the last resident column's y and
+ * passive set (the continuity of Sec. 2's warm start).  FP64 input is
+ * rounded to FP32 in NMF_PREC_MIXED handles.  Returns NMF_ENUMERIC (data
+ * stored, handle usable) if a value is NaN or Inf; NMF_EINVAL for ld < n. */
+nmf_status nmf_append_columns(nmf_handle *h, const void *cols, int64_t ncols, int64_t ld,
+                              int32_t dtype, int32_t on_device);
+
+/* Number of resident columns m. */
+int64_t nmf_num_columns(const nmf_handle *h);
+
+/* Set the iterate: X (n x k row-major) and Y (k x m column-major for the m
+ * resident columns, FP64).  Negative entries are set to 0.  Runs one priming
+ * pass over M so that the first sweep can report the iterate's KKT error.
+ * NMF_ESTATE if no column is resident. */
+nmf_status nmf_set_factors(nmf_handle *h, const double *X, const double *Y, int32_t on_device);
+
+/* Copy the current iterate out (X n x k, Y k x m, masks may be NULL).
+ * Synchronises the stream. */
+nmf_status nmf_get_factors(nmf_handle *h, double *X, double *Y, uint32_t *xmask, uint32_t *ymask,
+                           int32_t on_device);
+
+/* Run ANLS sweeps (Alg. "anls", Sec. 2; Y-update then X-update).  nsweeps > 0
+ * runs that many (fewer if a stopping test holds); nsweeps == 0 runs until
+ * the relative KKT target or the step tolerance is met, or max_sweeps
+ * (NMF_ENOTCONV).  The KKT error of iterate t is measured during sweep t from
+ * the Grams (no second read of M); when the target holds, the handle keeps
+ * iterate t.  stats (may be NULL) describes the last measured iterate; a
+ * non-NULL stats synchronises the stream. */
+nmf_status nmf_sweep(nmf_handle *h, int32_t nsweeps, nmf_stats *stats);
+
+/* NMF_PREC_MIXED handles: force the arithmetic of the following M passes
+ * (0 = FP32 contraction, 1 = FP64-accumulated contraction of the FP32 M,
+ * -1 = automatic: FP32 until the relative KKT error reaches mixed_switch or
+ * stalls, then FP64-accumulated).  NMF_PREC_FP64 handles ignore it. */
+nmf_status nmf_set_pass_mode(nmf_handle *h, int32_t mode);
+
+/* Objective and KKT error of the current iterate from one read-only,
+ * FP64-accumulated pass over M plus the Grams: f = 1/2||XY - M||^2,
+ * kkt_abs = max{||(min(graX,0), min(graY,0))||, ||(r o X, s o Y)||} (eq.
+ * "error" with mu = 0 and the duals of Sec. 5.1), kkt_rel = max{ first term /
+ * s_g, second term / (s_g max(max X, max Y)) } with s_g = ||M Y^T||_F +
+ * ||X^T M||_F.  Any output pointer may be NULL.  Synchronises the stream. */
+nmf_status nmf_objective_kkt(nmf_handle *h, double *f, double *kkt_abs, double *kkt_rel);
+
+/* Static description of a status code. */
+const char *nmf_status_string(nmf_status s);
+
+/* Detail of the handle's last failure ("" if none). */
+const char *nmf_last_error(const nmf_handle *h);
+
+/* Number of kernel launches the handle has issued so far (for accounting). */
+int64_t nmf_launch_count(const nmf_handle *h);
+
+/* Per-kernel device timing: with on = 1 every later sweep brackets its M
+ * pass and its row pass with CUDA events on the handle's stream; on = 0
+ * stops.  Each call resets the accumulated figures. */
+nmf_status nmf_set_timing(nmf_handle *h, int32_t on);
+
+/* Accumulated device time (ms) and launch counts of the M pass (ypass) and
+ * of the row pass (xpass) since nmf_set_timing(h, 1).  Synchronises the
+ * stream.  Any output pointer may be NULL. */
+nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launches,
+                          double *xpass_ms, int64_t *xpass_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMF_GB300_H */

@@ -1,0 +1,137 @@
+"""GB300 (sm_103a) library for the stage-1 ANLS sweep of two-stage streaming
+NMF (Gu, Du & Billinge, arXiv 2101.08431).
+
+The Python layer marshals arguments to the C ABI of ``include/nmf.h``; every
+step of the method runs in the library's CUDA kernels.  ``StreamingNMF`` is a
+convenience wrapper around one handle; ``_native`` exposes the raw functions
+under their C names.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+from ._native import (NMF_DTYPE_F32, NMF_DTYPE_F64, NMF_PREC_FP64, NMF_PREC_MIXED, NMF_WARM_COLD,
+                      NMF_WARM_PREV, NMFError, check, load, nmf_config, nmf_stats)
+
+__all__ = ["StreamingNMF", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
+           "NMF_PREC_MIXED", "NMF_DTYPE_F32", "NMF_DTYPE_F64", "NMF_WARM_COLD", "NMF_WARM_PREV"]
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class StreamingNMF:
+    """One problem: min 1/2||XY - M||^2, X, Y >= 0, columns of M appended over time."""
+
+    def __init__(self, n, k, m_capacity, prec=NMF_PREC_MIXED, kkt_target=1e-8, stol=0.0,
+                 mixed_switch=1e-6, max_sweeps=100000, warm_start=NMF_WARM_PREV, stream=None):
+        self.lib = load()
+        cfg = nmf_config()
+        self.lib.nmf_config_init(C.byref(cfg))
+        cfg.n, cfg.m_capacity, cfg.k, cfg.prec = int(n), int(m_capacity), int(k), int(prec)
+        cfg.kkt_target, cfg.stol, cfg.mixed_switch = float(kkt_target), float(stol), float(mixed_switch)
+        cfg.max_sweeps, cfg.warm_start = int(max_sweeps), int(warm_start)
+        cfg.cuda_stream = stream
+        h = C.c_void_p()
+        check(self.lib.nmf_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.n, self.k, self.m_capacity = int(n), int(k), int(m_capacity)
+
+    # -- data -------------------------------------------------------------------
+    def append_columns(self, cols):
+        """cols: n x c (numpy or torch, float32/float64); any strides with unit row stride."""
+        if isinstance(cols, np.ndarray):
+            a = np.asfortranarray(cols)
+            dtype = NMF_DTYPE_F32 if a.dtype == np.float32 else NMF_DTYPE_F64
+            if a.dtype not in (np.float32, np.float64):
+                a = np.asfortranarray(a, dtype=np.float64)
+                dtype = NMF_DTYPE_F64
+            ptr, dev, ncols, ld = a.ctypes.data, 0, a.shape[1], a.shape[0]
+            keep = a
+        else:   # torch tensor, column-major view expected: stride (1, ld)
+            t = cols
+            if t.stride(0) != 1:
+                t = t.t().contiguous().t()
+            dtype = NMF_DTYPE_F32 if str(t.dtype) == "torch.float32" else NMF_DTYPE_F64
+            ptr, dev, ncols, ld = t.data_ptr(), int(t.is_cuda), t.shape[1], t.stride(1)
+            keep = t
+        st = self.lib.nmf_append_columns(self.h, C.c_void_p(ptr), int(ncols), int(max(ld, 1)), dtype, dev)
+        del keep
+        return check(st, self.h)
+
+    @property
+    def m(self):
+        return int(self.lib.nmf_num_columns(self.h))
+
+    def set_factors(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.asfortranarray(Y, dtype=np.float64)
+        check(self.lib.nmf_set_factors(self.h, C.c_void_p(X.ctypes.data), C.c_void_p(Y.ctypes.data), 0),
+              self.h)
+
+    def get_factors(self):
+        m = self.m
+        X = np.zeros((self.n, self.k))
+        Y = np.zeros((self.k, m), order="F")
+        xm = np.zeros(self.n, dtype=np.uint32)
+        ym = np.zeros(m, dtype=np.uint32)
+        check(self.lib.nmf_get_factors(self.h, C.c_void_p(X.ctypes.data), C.c_void_p(Y.ctypes.data),
+                                       C.c_void_p(xm.ctypes.data), C.c_void_p(ym.ctypes.data), 0), self.h)
+        return X, np.ascontiguousarray(Y), xm, ym
+
+    # -- iteration --------------------------------------------------------------
+    def set_pass_mode(self, mode):
+        check(self.lib.nmf_set_pass_mode(self.h, int(mode)), self.h)
+
+    def sweep(self, nsweeps=1, want_stats=True, allow_notconv=False):
+        st = nmf_stats()
+        s = self.lib.nmf_sweep(self.h, int(nsweeps), C.byref(st) if want_stats else None)
+        if allow_notconv and s == _native.NMF_ENOTCONV:
+            return st.as_dict()
+        check(s, self.h)
+        return st.as_dict() if want_stats else None
+
+    def objective_kkt(self):
+        f, e, r = C.c_double(), C.c_double(), C.c_double()
+        check(self.lib.nmf_objective_kkt(self.h, C.byref(f), C.byref(e), C.byref(r)), self.h)
+        return {"f": f.value, "kkt_abs": e.value, "kkt_rel": r.value}
+
+    def set_timing(self, on=True):
+        check(self.lib.nmf_set_timing(self.h, int(bool(on))), self.h)
+
+    def get_timing(self):
+        ym, xm = C.c_double(), C.c_double()
+        yl, xl = C.c_int64(), C.c_int64()
+        check(self.lib.nmf_get_timing(self.h, C.byref(ym), C.byref(yl), C.byref(xm), C.byref(xl)), self.h)
+        return {"ypass_ms": ym.value, "ypass_launches": yl.value, "xpass_ms": xm.value,
+                "xpass_launches": xl.value}
+
+    @property
+    def launches(self):
+        return int(self.lib.nmf_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

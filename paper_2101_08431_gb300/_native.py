@@ -1,0 +1,100 @@
+"""ctypes declarations of the C ABI in ``include/nmf.h`` (same names).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Loading fails loudly if the library has not been built; there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnmf_gb300.so")
+
+NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ECUDA, NMF_ENOTCONV, NMF_ETIMEOUT, NMF_ECAPACITY, \
+    NMF_ENUMERIC, NMF_ESTATE = range(9)
+NMF_PREC_FP64, NMF_PREC_MIXED = 0, 1
+NMF_DTYPE_F64, NMF_DTYPE_F32 = 0, 1
+NMF_WARM_COLD, NMF_WARM_PREV = 0, 1
+
+# every symbol declared in include/nmf.h
+EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns", "nmf_num_columns",
+           "nmf_set_factors", "nmf_get_factors", "nmf_sweep", "nmf_set_pass_mode",
+           "nmf_objective_kkt", "nmf_status_string", "nmf_last_error", "nmf_launch_count",
+           "nmf_set_timing", "nmf_get_timing")
+
+
+class nmf_config(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m_capacity", C.c_int64), ("k", C.c_int32), ("prec", C.c_int32),
+                ("stol", C.c_double), ("kkt_target", C.c_double), ("mixed_switch", C.c_double),
+                ("max_sweeps", C.c_int32), ("warm_start", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class nmf_stats(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("iter", C.c_int32), ("converged", C.c_int32),
+                ("fp64_sweeps", C.c_int32), ("f", C.c_double), ("kkt_abs", C.c_double),
+                ("kkt_rel", C.c_double), ("step_rel", C.c_double), ("changed_cols", C.c_int64),
+                ("changed_rows", C.c_int64), ("nnls_notconv", C.c_int64), ("measured_iter", C.c_int32),
+                ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+class NMFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the built library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("the CUDA library %s has not been built; run "
+                          "`python -m paper_2101_08431_gb300.build` (nvcc required)" % path)
+    L = C.CDLL(path)
+    H = C.c_void_p
+    L.nmf_config_init.argtypes = [C.POINTER(nmf_config)]
+    L.nmf_config_init.restype = None
+    L.nmf_create.argtypes = [C.POINTER(nmf_config), C.POINTER(H)]
+    L.nmf_destroy.argtypes = [H]
+    L.nmf_append_columns.argtypes = [H, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32]
+    L.nmf_num_columns.argtypes = [H]
+    L.nmf_num_columns.restype = C.c_int64
+    L.nmf_set_factors.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32]
+    L.nmf_get_factors.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+    L.nmf_sweep.argtypes = [H, C.c_int32, C.POINTER(nmf_stats)]
+    L.nmf_set_pass_mode.argtypes = [H, C.c_int32]
+    L.nmf_objective_kkt.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
+    L.nmf_status_string.argtypes = [C.c_int]
+    L.nmf_status_string.restype = C.c_char_p
+    L.nmf_last_error.argtypes = [H]
+    L.nmf_last_error.restype = C.c_char_p
+    L.nmf_launch_count.argtypes = [H]
+    L.nmf_launch_count.restype = C.c_int64
+    L.nmf_set_timing.argtypes = [H, C.c_int32]
+    L.nmf_get_timing.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    for name in EXPORTS:
+        if name not in ("nmf_config_init", "nmf_num_columns", "nmf_status_string", "nmf_last_error",
+                        "nmf_launch_count"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def check(status: int, handle=None):
+    if status != NMF_OK:
+        L = load()
+        detail = L.nmf_last_error(handle).decode() if handle else ""
+        raise NMFError(status, "%s%s" % (L.nmf_status_string(status).decode(),
+                                         (": " + detail) if detail else ""))
+    return status

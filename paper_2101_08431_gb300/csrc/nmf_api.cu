@@ -1,0 +1,755 @@
+// C ABI of the GB300 streaming-NMF library (declared in include/nmf.h):
+// handle life cycle, the resident column ring, priming, the sweep driver with
+// the mixed-precision schedule, and the read-only objective / KKT pass.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "../../include/nmf.h"
+#include "nmf_launch.cuh"
+
+using namespace nmfgb;
+
+namespace {
+
+constexpr int CHUNK = 32;                  // sweeps between host checks
+constexpr int STALL_CHUNKS = 8;            // MIXED: FP32 passes without progress before switching
+constexpr int APPEND_STAGE_COLS = 256;     // host-to-device staging width
+
+int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+// Copy one staged column block into the ring (converting the element type),
+// zero the padding rows, record ||M_{:,j}||^2 and seed y_j from *seed.
+template <typename TS, typename TM>
+__global__ void append_kernel(const TS* __restrict__ src, long long ld_src, int ncols, TM* M, int ld,
+                              int n, int mcap, int first_phys, double* colsq, const double* seed,
+                              const uint32_t* seed_mask, DevState* st, double* Y0, double* Y1,
+                              uint32_t* ym0, uint32_t* ym1, int k, unsigned* nonfinite) {
+  const int c = blockIdx.x;
+  if (c >= ncols) return;
+  int phys = first_phys + c;
+  if (phys >= mcap) phys -= mcap;
+  const TS* s = src + (size_t)c * ld_src;
+  TM* d = M + (size_t)phys * ld;
+  double acc = 0.0;
+  unsigned bad = 0;
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    TM v = TM(0);
+    if (i < n) {
+      v = (TM)s[i];
+      if (!isfinite((double)v)) ++bad;
+    }
+    d[i] = v;
+    acc = fma((double)v, (double)v, acc);
+  }
+  __shared__ double red[32];
+  acc = warp_sum(acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  if (bad) atomicAdd(nonfinite, bad);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    colsq[phys] = t;
+  }
+  if (threadIdx.x < k) {
+    const int cur = st->iter & 1;
+    double* Y = cur ? Y1 : Y0;
+    uint32_t* ym = cur ? ym1 : ym0;
+    Y[(size_t)phys * k + threadIdx.x] = seed ? seed[threadIdx.x] : 0.0;
+    if (threadIdx.x == 0) ym[phys] = seed_mask ? *seed_mask : 0u;
+  }
+}
+
+// seed <- y and mask of the physical column `phys` of the current buffers
+__global__ void seed_kernel(DevState* st, const double* Y0, const double* Y1, const uint32_t* ym0,
+                            const uint32_t* ym1, int phys, int k, double* seed, uint32_t* seed_mask) {
+  const int cur = st->iter & 1;
+  const double* Y = cur ? Y1 : Y0;
+  const uint32_t* ym = cur ? ym1 : ym0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) seed[a] = Y[(size_t)phys * k + a];
+  if (threadIdx.x == 0) *seed_mask = ym[phys];
+}
+
+// ||M||^2 of the resident window (fixed order) and invalidation of the X-half
+// terms of the current iterate (P = M Y^T changed).
+__global__ void msq_kernel(DevState* st, const double* colsq, int head, int m, int mcap) {
+  __shared__ double red[256];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    int ph = head + j;
+    if (ph >= mcap) ph -= mcap;
+    t += colsq[ph];
+  }
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->msq = red[0];
+    st->xiter[0][XT_VALID] = 0.0;
+    st->xiter[1][XT_VALID] = 0.0;
+  }
+}
+
+// Statistics of the current iterate after a read-only (MODE_KKT) M pass.
+__global__ void kkt_stats_kernel(Problem p, int Q, double* out) {
+  __shared__ double yfin[NYT];
+  const int tid = threadIdx.x;
+  DevState* st = p.st;
+  if (tid < NYT) {
+    double r = 0.0;
+    for (int qq = 0; qq < Q; ++qq) {
+      const double w = p.Yterms[(size_t)qq * NYT + tid];
+      r = (tid == YT_YMAX) ? fmax(r, w) : r + w;
+    }
+    yfin[tid] = r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int iter = st->iter;
+    combine_stats(yfin, st->xiter[iter & 1], st->msq, -1.0, iter, p.fp64_pass, out);
+  }
+}
+
+__global__ void clamp_kernel(double* v, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!(v[i] > 0.0)) v[i] = 0.0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct nmf_handle {
+  nmf_config cfg{};
+  int dev = 0, nsm = 0, smem_optin = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n = 0, ld = 0, k = 0, mcap = 0, m = 0, head = 0;
+  bool store_f32 = true;
+  void* dM = nullptr;
+  double* dX[2] = {nullptr, nullptr};
+  float* dX32[2] = {nullptr, nullptr};
+  double* dY[2] = {nullptr, nullptr};
+  uint32_t* dYm[2] = {nullptr, nullptr};
+  uint32_t* dXm[2] = {nullptr, nullptr};
+  double* dG = nullptr;
+  double* dColsq = nullptr;
+  void* dPpart = nullptr;
+  double* dHpart = nullptr;
+  double* dYterms = nullptr;
+  double* dXpart = nullptr;
+  DevState* dSt = nullptr;
+  double* dKkt = nullptr;
+  double* dSeed = nullptr;
+  uint32_t* dSeedMask = nullptr;
+  unsigned* dNonfinite = nullptr;
+  void* dStage = nullptr;
+  size_t stage_bytes = 0;
+  DevState* hSt = nullptr;      // pinned mirror
+  double* hKkt = nullptr;
+  unsigned* hNonfinite = nullptr;
+  int nxblk = 0;
+  bool factors_set = false;
+  nmf_status poisoned = NMF_OK;
+  int phase = 0;                // MIXED: 0 FP32 passes, 1 FP64-accumulated passes
+  int forced_mode = -1;
+  double best_rel = -1.0;       // MIXED schedule: best FP32-pass relative KKT so far
+  int chunks_since_best = 0;
+  bool snap_valid = false;      // hSt mirrors the device state
+  int64_t launches = 0;
+  std::string last_error;
+  KernelSet ks[NVAR]{};
+  bool has[NVAR] = {false, false, false};
+  int max_clusters[NVAR][4] = {};   // per variant, cluster size 1, 2, 4, 8 (full smem)
+  // per-kernel timing (event triplets around each sweep's two launches)
+  bool timing = false;
+  static constexpr int NEV = 512;
+  cudaEvent_t ev[NEV][3] = {};
+  int nev = 0;
+  double y_ms = 0.0, x_ms = 0.0;
+  int64_t y_launches = 0, x_launches = 0;
+};
+
+namespace {
+
+nmf_status fail(nmf_handle* h, nmf_status s, const std::string& msg) {
+  if (h) {
+    h->last_error = msg;
+    if (s == NMF_ECUDA || s == NMF_ETIMEOUT) h->poisoned = s;
+  }
+  return s;
+}
+
+#define CUDA_TRY(h, expr)                                                           \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail((h), NMF_ECUDA, std::string(#expr ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool make_plan(const nmf_handle* h, int var, YPlan* L) {
+  const KernelSet& K = h->ks[var];
+  const int rmax = K.RPT * 512;
+  int C = 1, R = 0;
+  for (C = 1; C <= 8; C <<= 1) {
+    R = round_up((h->ld + C - 1) / C, 32);
+    if (R <= rmax) break;
+  }
+  if (C > 8) return false;
+  int Q = std::max(1, std::min(h->nsm / C, std::max(h->m, 1)));
+  const int cpc = (std::max(h->m, 1) + Q - 1) / Q;
+  const int ntiles = (cpc + K.TJ - 1) / K.TJ;
+  const size_t stage = (size_t)K.TJ * R * K.tm_size;
+  long long S = ((long long)h->smem_optin - (long long)K.small_bytes) / (long long)stage;
+  if (S > 8) S = 8;
+  if (S > ntiles) S = ntiles;
+  if (S < 1) return false;
+  const size_t smem = K.small_bytes + (size_t)S * stage;
+  // persistent grid: never more clusters than the device holds at once
+  const int ci = C == 1 ? 0 : (C == 2 ? 1 : (C == 4 ? 2 : 3));
+  const int fit = h->max_clusters[var][ci];
+  if (fit > 0 && Q > fit) Q = fit;
+  L->C = C;
+  L->R = R;
+  L->Q = Q;
+  L->S = (int)S;
+  L->smem = smem;
+  static const bool debug_plan = std::getenv("NMF_DEBUG_PLAN") != nullptr;
+  if (debug_plan)
+    std::fprintf(stderr, "nmf plan: variant %d C=%d R=%d Q=%d S=%d smem=%zu fit=%d\n", var, C, R, Q,
+                 (int)S, smem, fit);
+  return true;
+}
+
+Problem make_problem(const nmf_handle* h, int var) {
+  Problem p{};
+  p.n = h->n;
+  p.m = h->m;
+  p.k = h->k;
+  p.ld = h->ld;
+  p.mcap = h->mcap;
+  p.head = h->head;
+  p.M = h->dM;
+  for (int b = 0; b < 2; ++b) {
+    p.X[b] = h->dX[b];
+    p.X32[b] = h->dX32[b];
+    p.Y[b] = h->dY[b];
+    p.ymask[b] = h->dYm[b];
+    p.xmask[b] = h->dXm[b];
+  }
+  p.G = h->dG;
+  p.colsq = h->dColsq;
+  p.Ppart = h->dPpart;
+  p.Hpart = h->dHpart;
+  p.Yterms = h->dYterms;
+  p.Xpart = h->dXpart;
+  p.st = h->dSt;
+  p.warm = h->cfg.warm_start != NMF_WARM_COLD;
+  p.fp64_pass = var != VAR_F32;
+  const bool final_phase = !(h->store_f32 && var == VAR_F32);
+  p.kkt_target = final_phase ? h->cfg.kkt_target : 0.0;
+  p.stol = final_phase ? h->cfg.stol : 0.0;
+  return p;
+}
+
+// Fold recorded event triplets into the timing totals (synchronises them).
+nmf_status drain_timing(nmf_handle* h) {
+  for (int i = 0; i < h->nev; ++i) {
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(h, cudaEventSynchronize(h->ev[i][2]));
+    CUDA_TRY(h, cudaEventElapsedTime(&a, h->ev[i][0], h->ev[i][1]));
+    CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[i][1], h->ev[i][2]));
+    h->y_ms += a;
+    h->x_ms += b;
+  }
+  h->y_launches += h->nev;
+  h->x_launches += h->nev;
+  h->nev = 0;
+  return NMF_OK;
+}
+
+// One sweep (M pass + row pass) or, with mode PRIME, the priming pair.
+nmf_status launch_pair(nmf_handle* h, int var, int mode) {
+  YPlan L;
+  if (!make_plan(h, var, &L)) return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  Problem p = make_problem(h, var);
+  const bool timed = h->timing && mode == MODE_SWEEP;
+  if (timed && h->nev == nmf_handle::NEV) {
+    nmf_status s = drain_timing(h);
+    if (s != NMF_OK) return s;
+  }
+  if (timed) {
+    if (!h->ev[h->nev][0])
+      for (int j = 0; j < 3; ++j) CUDA_TRY(h, cudaEventCreate(&h->ev[h->nev][j]));
+    CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][0], h->stream));
+  }
+  CUDA_TRY(h, h->ks[var].ypass(p, mode, L, h->stream));
+  if (timed) CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][1], h->stream));
+  CUDA_TRY(h, h->ks[var].xpass(p, mode, L.Q, h->nxblk, h->stream));
+  if (timed) {
+    CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][2], h->stream));
+    h->nev++;
+  }
+  h->launches += 2;
+  return NMF_OK;
+}
+
+int variant_for(const nmf_handle* h) {
+  if (!h->store_f32) return VAR_F64;
+  if (h->forced_mode == 0) return VAR_F32;
+  if (h->forced_mode == 1) return VAR_REF;
+  return h->phase ? VAR_REF : VAR_F32;
+}
+
+nmf_status read_state(nmf_handle* h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->hSt, h->dSt, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->snap_valid = true;
+  if (h->hSt->err & ERR_TIMEOUT) return fail(h, NMF_ETIMEOUT, "a device wait exceeded its bound");
+  if (h->hSt->err & ERR_NONFINITE) return fail(h, NMF_ENUMERIC, "non-finite value in a sweep");
+  return NMF_OK;
+}
+
+void fill_stats(const nmf_handle* h, int measured, int sweeps, int fp64_sweeps, nmf_stats* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->sweeps = sweeps;
+  out->iter = h->hSt->iter;
+  out->fp64_sweeps = fp64_sweeps;
+  out->converged = h->hSt->done ? h->hSt->stop_reason : 0;
+  out->measured_iter = measured;
+  if (measured < 0) return;
+  const double* r = h->hSt->stats[measured % STAT_CAP];
+  out->f = r[ST_F];
+  out->kkt_abs = r[ST_EABS];
+  out->kkt_rel = r[ST_VALID] > 0.0 ? r[ST_REL] : -1.0;
+  out->step_rel = r[ST_STEP];
+  out->changed_cols = (int64_t)r[ST_CHANGED_COLS];
+  out->changed_rows = (int64_t)r[ST_CHANGED_ROWS];
+  out->nnls_notconv = (int64_t)r[ST_NOTCONV];
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void nmf_config_init(nmf_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->prec = NMF_PREC_MIXED;
+  cfg->stol = 0.0;
+  cfg->kkt_target = 1e-8;
+  cfg->mixed_switch = 1e-6;
+  cfg->max_sweeps = 100000;
+  cfg->warm_start = NMF_WARM_PREV;
+  cfg->cuda_stream = nullptr;
+}
+
+const char* nmf_status_string(nmf_status s) {
+  switch (s) {
+    case NMF_OK: return "ok";
+    case NMF_EINVAL: return "invalid argument";
+    case NMF_ENOMEM: return "out of memory";
+    case NMF_ECUDA: return "CUDA error";
+    case NMF_ENOTCONV: return "not converged";
+    case NMF_ETIMEOUT: return "device wait timed out";
+    case NMF_ECAPACITY: return "capacity exceeded";
+    case NMF_ENUMERIC: return "non-finite value";
+    case NMF_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* nmf_last_error(const nmf_handle* h) { return h ? h->last_error.c_str() : ""; }
+
+int64_t nmf_launch_count(const nmf_handle* h) { return h ? h->launches : 0; }
+
+int64_t nmf_num_columns(const nmf_handle* h) { return h ? h->m : 0; }
+
+nmf_status nmf_destroy(nmf_handle* h) {
+  if (!h) return NMF_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < nmf_handle::NEV; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
+  void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dY[0], h->dY[1],
+                   h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dColsq, h->dPpart,
+                   h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
+                   h->dNonfinite, h->dStage};
+  for (void* p : dptrs)
+    if (p) cudaFree(p);
+  if (h->hSt) cudaFreeHost(h->hSt);
+  if (h->hKkt) cudaFreeHost(h->hKkt);
+  if (h->hNonfinite) cudaFreeHost(h->hNonfinite);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return NMF_OK;
+}
+
+nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
+  if (!cfg || !out) return NMF_EINVAL;
+  *out = nullptr;
+  const int k = cfg->k;
+  if (cfg->n < 1 || cfg->n > (1 << 20) || cfg->m_capacity < 1 || cfg->m_capacity > (1 << 24) ||
+      !((k >= 1 && k <= 8) || k == 16) || (cfg->prec != NMF_PREC_FP64 && cfg->prec != NMF_PREC_MIXED))
+    return NMF_EINVAL;
+  nmf_handle* h = new (std::nothrow) nmf_handle();
+  if (!h) return NMF_ENOMEM;
+  h->cfg = *cfg;
+  h->n = (int)cfg->n;
+  h->k = k;
+  h->mcap = (int)cfg->m_capacity;
+  h->ld = round_up(h->n, 32);
+  h->store_f32 = cfg->prec == NMF_PREC_MIXED;
+  h->nxblk = (h->n + XTraits<1>::RB - 1) / XTraits<1>::RB;
+  auto bail = [&](nmf_status s, const char* msg) {
+    std::string m = msg;
+    nmf_destroy(h);
+    (void)m;
+    return s;
+  };
+  if (cudaGetDevice(&h->dev) != cudaSuccess) return bail(NMF_ECUDA, "no CUDA device");
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
+  cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+  h->has[VAR_F32] = get_kernels_f32(k, &h->ks[VAR_F32]);
+  h->has[VAR_REF] = get_kernels_ref(k, &h->ks[VAR_REF]);
+  h->has[VAR_F64] = get_kernels_f64(k, &h->ks[VAR_F64]);
+  for (int v = 0; v < NVAR; ++v)
+    if (h->has[v])
+      for (int ci = 0; ci < 4; ++ci)
+        h->max_clusters[v][ci] = h->ks[v].max_clusters(1 << ci, (size_t)h->smem_optin);
+  {
+    // every variant this handle may run must have a plan for n
+    const int need[2] = {h->store_f32 ? VAR_F32 : VAR_F64, h->store_f32 ? VAR_REF : VAR_F64};
+    for (int v : need) {
+      YPlan L;
+      int msave = h->m;
+      h->m = h->mcap;
+      const bool ok = h->has[v] && make_plan(h, v, &L);
+      h->m = msave;
+      if (!ok) return bail(NMF_EINVAL, "n too large for the kernels of this precision");
+    }
+  }
+  if (cfg->cuda_stream) {
+    h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(NMF_ECUDA, "stream creation failed");
+    h->own_stream = true;
+  }
+  const size_t nk = (size_t)h->n * k, mk = (size_t)h->mcap * k;
+  const int Qmax = h->nsm;
+  bool ok = true;
+  ok &= cudaMalloc(&h->dM, (size_t)h->ld * h->mcap * (h->store_f32 ? 4 : 8)) == cudaSuccess;
+  for (int b = 0; b < 2; ++b) {
+    ok &= dalloc(&h->dX[b], nk) == cudaSuccess;
+    ok &= dalloc(&h->dX32[b], nk) == cudaSuccess;
+    ok &= dalloc(&h->dY[b], mk) == cudaSuccess;
+    ok &= dalloc(&h->dYm[b], h->mcap) == cudaSuccess;
+    ok &= dalloc(&h->dXm[b], h->n) == cudaSuccess;
+  }
+  ok &= dalloc(&h->dG, (size_t)k * k) == cudaSuccess;
+  ok &= dalloc(&h->dColsq, h->mcap) == cudaSuccess;
+  ok &= cudaMalloc(&h->dPpart, (size_t)Qmax * h->ld * k * 8) == cudaSuccess;
+  ok &= dalloc(&h->dHpart, (size_t)Qmax * k * k) == cudaSuccess;
+  ok &= dalloc(&h->dYterms, (size_t)Qmax * NYT) == cudaSuccess;
+  ok &= dalloc(&h->dXpart, (size_t)h->nxblk * (k * k + NXT)) == cudaSuccess;
+  ok &= dalloc(&h->dSt, 1) == cudaSuccess;
+  ok &= dalloc(&h->dKkt, NSTAT) == cudaSuccess;
+  ok &= dalloc(&h->dSeed, KMAX) == cudaSuccess;
+  ok &= dalloc(&h->dSeedMask, 1) == cudaSuccess;
+  ok &= dalloc(&h->dNonfinite, 1) == cudaSuccess;
+  ok &= cudaMallocHost(&h->hSt, sizeof(DevState)) == cudaSuccess;
+  ok &= cudaMallocHost(&h->hKkt, sizeof(double) * NSTAT) == cudaSuccess;
+  ok &= cudaMallocHost(&h->hNonfinite, sizeof(unsigned)) == cudaSuccess;
+  if (!ok) return bail(NMF_ENOMEM, "device allocation failed");
+  cudaMemsetAsync(h->dM, 0, (size_t)h->ld * h->mcap * (h->store_f32 ? 4 : 8), h->stream);
+  cudaMemsetAsync(h->dSt, 0, sizeof(DevState), h->stream);
+  cudaMemsetAsync(h->dColsq, 0, sizeof(double) * h->mcap, h->stream);
+  for (int b = 0; b < 2; ++b) {
+    cudaMemsetAsync(h->dY[b], 0, sizeof(double) * mk, h->stream);
+    cudaMemsetAsync(h->dYm[b], 0, sizeof(uint32_t) * h->mcap, h->stream);
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(NMF_ECUDA, "initialisation failed");
+  *out = h;
+  return NMF_OK;
+}
+
+nmf_status nmf_append_columns(nmf_handle* h, const void* cols, int64_t ncols, int64_t ld,
+                              int32_t dtype, int32_t on_device) {
+  if (!h) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (ncols < 0 || (ncols > 0 && !cols) || ld < h->n || (dtype != NMF_DTYPE_F32 && dtype != NMF_DTYPE_F64))
+    return fail(h, NMF_EINVAL, "bad append arguments");
+  if (ncols == 0) return NMF_OK;
+  const size_t esz = dtype == NMF_DTYPE_F32 ? 4 : 8;
+  const char* src = static_cast<const char*>(cols);
+  if (ncols > h->mcap) {          // only the newest m_capacity columns can stay
+    src += (size_t)(ncols - h->mcap) * ld * esz;
+    ncols = h->mcap;
+  }
+  // seed for the new columns: the newest resident column (before eviction)
+  const bool have_seed = h->m > 0;
+  if (have_seed) {
+    const int seed_phys = wrap_col(h->head, h->m - 1, h->mcap);
+    seed_kernel<<<1, 32, 0, h->stream>>>(h->dSt, h->dY[0], h->dY[1], h->dYm[0], h->dYm[1], seed_phys,
+                                         h->k, h->dSeed, h->dSeedMask);
+    h->launches++;
+  }
+  const int first_phys = wrap_col(h->head, h->m, h->mcap);   // slot of the first new column
+  const int evict = std::max(0, h->m + (int)ncols - h->mcap);
+  CUDA_TRY(h, cudaMemsetAsync(h->dNonfinite, 0, sizeof(unsigned), h->stream));
+  auto run = [&](const void* s, long long lds, int nc, int fp) -> cudaError_t {
+    if (h->store_f32) {
+      if (dtype == NMF_DTYPE_F32)
+        append_kernel<float, float><<<nc, 256, 0, h->stream>>>(
+            (const float*)s, lds, nc, (float*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
+            have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+      else
+        append_kernel<double, float><<<nc, 256, 0, h->stream>>>(
+            (const double*)s, lds, nc, (float*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
+            have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+    } else {
+      if (dtype == NMF_DTYPE_F32)
+        append_kernel<float, double><<<nc, 256, 0, h->stream>>>(
+            (const float*)s, lds, nc, (double*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
+            have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+      else
+        append_kernel<double, double><<<nc, 256, 0, h->stream>>>(
+            (const double*)s, lds, nc, (double*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
+            have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+    }
+    h->launches++;
+    return cudaGetLastError();
+  };
+  if (on_device) {
+    CUDA_TRY(h, run(src, ld, (int)ncols, first_phys));
+  } else {
+    const size_t need = (size_t)h->n * APPEND_STAGE_COLS * 8;
+    if (h->stage_bytes < need) {
+      if (h->dStage) cudaFree(h->dStage);
+      h->dStage = nullptr;
+      h->stage_bytes = 0;
+      CUDA_TRY(h, cudaMalloc(&h->dStage, need));
+      h->stage_bytes = need;
+    }
+    for (int64_t c0 = 0; c0 < ncols; c0 += APPEND_STAGE_COLS) {
+      const int nc = (int)std::min<int64_t>(APPEND_STAGE_COLS, ncols - c0);
+      CUDA_TRY(h, cudaMemcpy2DAsync(h->dStage, (size_t)h->n * esz, src + (size_t)c0 * ld * esz,
+                                    (size_t)ld * esz, (size_t)h->n * esz, nc, cudaMemcpyHostToDevice,
+                                    h->stream));
+      CUDA_TRY(h, run(h->dStage, h->n, nc, wrap_col(first_phys, (int)c0 % h->mcap, h->mcap)));
+    }
+  }
+  h->head = wrap_col(h->head, evict % h->mcap, h->mcap);
+  h->m = h->m + (int)ncols - evict;
+  msq_kernel<<<1, 256, 0, h->stream>>>(h->dSt, h->dColsq, h->head, h->m, h->mcap);
+  h->launches++;
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemcpyAsync(h->hNonfinite, h->dNonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (*h->hNonfinite) return fail(h, NMF_ENUMERIC, "appended data contain NaN or Inf");
+  return NMF_OK;
+}
+
+nmf_status nmf_set_factors(nmf_handle* h, const double* X, const double* Y, int32_t on_device) {
+  if (!h || !X || !Y) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (h->m < 1) return fail(h, NMF_ESTATE, "no resident column");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // fresh iterate 0 in buffers 0 (keep ||M||^2)
+  CUDA_TRY(h, cudaMemsetAsync(h->dSt, 0, sizeof(DevState), h->stream));
+  msq_kernel<<<1, 256, 0, h->stream>>>(h->dSt, h->dColsq, h->head, h->m, h->mcap);
+  h->launches++;
+  const size_t k = h->k;
+  CUDA_TRY(h, cudaMemcpyAsync(h->dX[0], X, sizeof(double) * h->n * k, kind, h->stream));
+  const int first = std::min(h->m, h->mcap - h->head);
+  CUDA_TRY(h, cudaMemcpyAsync(h->dY[0] + (size_t)h->head * k, Y, sizeof(double) * first * k, kind,
+                              h->stream));
+  if (first < h->m)
+    CUDA_TRY(h, cudaMemcpyAsync(h->dY[0], Y + (size_t)first * k, sizeof(double) * (h->m - first) * k,
+                                kind, h->stream));
+  clamp_kernel<<<64, 256, 0, h->stream>>>(h->dX[0], (long long)h->n * k);
+  clamp_kernel<<<64, 256, 0, h->stream>>>(h->dY[0], (long long)h->mcap * k);
+  h->launches += 2;
+  CUDA_TRY(h, cudaGetLastError());
+  h->phase = 0;
+  h->best_rel = -1.0;
+  h->chunks_since_best = 0;
+  nmf_status s = launch_pair(h, h->store_f32 ? VAR_REF : VAR_F64, MODE_PRIME);
+  if (s != NMF_OK) return s;
+  s = read_state(h);
+  if (s != NMF_OK) return s;
+  h->factors_set = true;
+  return NMF_OK;
+}
+
+nmf_status nmf_get_factors(nmf_handle* h, double* X, double* Y, uint32_t* xmask, uint32_t* ymask,
+                           int32_t on_device) {
+  if (!h) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (!h->factors_set) return fail(h, NMF_ESTATE, "factors not set");
+  nmf_status s = read_state(h);
+  if (s != NMF_OK && s != NMF_ENUMERIC) return s;
+  const int cur = h->hSt->iter & 1;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t k = h->k;
+  if (X) CUDA_TRY(h, cudaMemcpyAsync(X, h->dX[cur], sizeof(double) * h->n * k, kind, h->stream));
+  if (xmask) CUDA_TRY(h, cudaMemcpyAsync(xmask, h->dXm[cur], sizeof(uint32_t) * h->n, kind, h->stream));
+  const int first = std::min(h->m, h->mcap - h->head);
+  if (Y) {
+    CUDA_TRY(h, cudaMemcpyAsync(Y, h->dY[cur] + (size_t)h->head * k, sizeof(double) * first * k, kind,
+                                h->stream));
+    if (first < h->m)
+      CUDA_TRY(h, cudaMemcpyAsync(Y + (size_t)first * k, h->dY[cur], sizeof(double) * (h->m - first) * k,
+                                  kind, h->stream));
+  }
+  if (ymask) {
+    CUDA_TRY(h, cudaMemcpyAsync(ymask, h->dYm[cur] + h->head, sizeof(uint32_t) * first, kind, h->stream));
+    if (first < h->m)
+      CUDA_TRY(h, cudaMemcpyAsync(ymask + first, h->dYm[cur], sizeof(uint32_t) * (h->m - first), kind,
+                                  h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return NMF_OK;
+}
+
+nmf_status nmf_set_timing(nmf_handle* h, int32_t on) {
+  if (!h) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  nmf_status s = drain_timing(h);
+  if (s != NMF_OK) return s;
+  h->timing = on != 0;
+  h->y_ms = h->x_ms = 0.0;
+  h->y_launches = h->x_launches = 0;
+  return NMF_OK;
+}
+
+nmf_status nmf_get_timing(nmf_handle* h, double* ypass_ms, int64_t* ypass_launches, double* xpass_ms,
+                          int64_t* xpass_launches) {
+  if (!h) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  nmf_status s = drain_timing(h);
+  if (s != NMF_OK) return s;
+  if (ypass_ms) *ypass_ms = h->y_ms;
+  if (ypass_launches) *ypass_launches = h->y_launches;
+  if (xpass_ms) *xpass_ms = h->x_ms;
+  if (xpass_launches) *xpass_launches = h->x_launches;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_pass_mode(nmf_handle* h, int32_t mode) {
+  if (!h || mode < -1 || mode > 1) return NMF_EINVAL;
+  h->forced_mode = mode;
+  return NMF_OK;
+}
+
+nmf_status nmf_sweep(nmf_handle* h, int32_t nsweeps, nmf_stats* stats) {
+  if (!h || nsweeps < 0) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (!h->factors_set) return fail(h, NMF_ESTATE, "factors not set");
+  CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
+  const bool until = nsweeps == 0;
+  const int cap = until ? std::max(1, h->cfg.max_sweeps) : nsweeps;
+  const bool adaptive = h->store_f32 && h->forced_mode < 0;
+  const bool need_checks = until || adaptive || stats;
+  nmf_status s = NMF_OK;
+  if (need_checks && !h->snap_valid) {
+    s = read_state(h);
+    if (s != NMF_OK) return s;
+  }
+  int iter_prev = h->hSt->iter;
+  int launched = 0, worked = 0, fp64_sweeps = 0, measured = -1;
+  bool done = false;
+  while (launched < cap) {
+    const int chunk = need_checks ? std::min(CHUNK, cap - launched) : cap - launched;
+    const int var = variant_for(h);
+    for (int i = 0; i < chunk; ++i) {
+      s = launch_pair(h, var, MODE_SWEEP);
+      if (s != NMF_OK) return s;
+    }
+    launched += chunk;
+    if (!need_checks) {
+      h->snap_valid = false;
+      break;
+    }
+    s = read_state(h);
+    if (s != NMF_OK) return s;
+    const int iter_now = h->hSt->iter;
+    done = h->hSt->done != 0;
+    const bool stop_kkt = done && h->hSt->stop_reason == 1;
+    const int w = (iter_now - iter_prev) + (stop_kkt ? 1 : 0);
+    worked += w;
+    if (var != VAR_F32) fp64_sweeps += w;
+    measured = stop_kkt ? iter_now : iter_now - 1;
+    iter_prev = iter_now;
+    if (done) break;
+    if (adaptive && h->phase == 0 && measured >= 0) {
+      // FP32 passes until the relative KKT error reaches mixed_switch, or
+      // until it has not improved by 2% over STALL_CHUNKS checks (the FP32
+      // contraction's floor), then FP64-accumulated passes.
+      const double* r = h->hSt->stats[measured % STAT_CAP];
+      const double rel = r[ST_VALID] > 0.0 ? r[ST_REL] : -1.0;
+      if (rel > 0.0) {
+        if (h->best_rel < 0.0 || rel < 0.98 * h->best_rel) {
+          h->best_rel = rel;
+          h->chunks_since_best = 0;
+        } else {
+          ++h->chunks_since_best;
+        }
+        if (rel <= h->cfg.mixed_switch || h->chunks_since_best >= STALL_CHUNKS) h->phase = 1;
+      }
+    }
+  }
+  if (stats) fill_stats(h, measured, worked, fp64_sweeps, stats);
+  if (until && !done) return fail(h, NMF_ENOTCONV, "sweep cap reached");
+  return NMF_OK;
+}
+
+nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* kkt_rel) {
+  if (!h) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (!h->factors_set) return fail(h, NMF_ESTATE, "factors not set");
+  const int var = h->store_f32 ? VAR_REF : VAR_F64;
+  YPlan L;
+  if (!make_plan(h, var, &L)) return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  Problem p = make_problem(h, var);
+  CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
+  CUDA_TRY(h, h->ks[var].ypass(p, MODE_KKT, L, h->stream));
+  kkt_stats_kernel<<<1, 32, 0, h->stream>>>(p, L.Q, h->dKkt);
+  h->launches += 2;
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemcpyAsync(h->hKkt, h->dKkt, sizeof(double) * NSTAT, cudaMemcpyDeviceToHost, h->stream));
+  nmf_status s = read_state(h);
+  if (s != NMF_OK) return s;
+  if (f) *f = h->hKkt[ST_F];
+  if (kkt_abs) *kkt_abs = h->hKkt[ST_EABS];
+  if (kkt_rel) *kkt_rel = h->hKkt[ST_VALID] > 0.0 ? h->hKkt[ST_REL] : -1.0;
+  return NMF_OK;
+}
+
+}  // extern "C"

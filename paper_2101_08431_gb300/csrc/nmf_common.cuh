@@ -1,0 +1,182 @@
+// Shared device-side definitions of the GB300 streaming-NMF library:
+// device state, launch descriptors, PTX wrappers (mbarrier, bulk async copy)
+// and fixed-order reductions.  Everything here is part of the CUDA path; the
+// CPU oracle has its own, separate implementation of the method.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nmfgb {
+
+namespace cg = cooperative_groups;
+
+constexpr int KMAX = 16;           // largest rank the kernels are built for
+constexpr int STAT_CAP = 64;       // per-iterate statistics ring
+constexpr int NSTAT = 16;          // doubles per statistics record
+constexpr int NYT = 10;            // KKT / objective terms of the Y half (per cluster)
+constexpr int NXT = 10;            // terms of the X half (per row block)
+constexpr int CACHE_N = 8;         // inverse-cache entries per CTA
+constexpr long long SPIN_LIMIT = 1ll << 26;   // bounded waits (about a second)
+
+// error bits in DevState::err
+constexpr unsigned ERR_TIMEOUT = 1u;
+constexpr unsigned ERR_NONFINITE = 2u;
+constexpr unsigned ERR_CONFIG = 4u;
+
+// Y-half terms, for the iterate (X_t, Y_t) entering a sweep:
+//   graY_j = G y_j - b_j with b_j = X_t^T M_{:,j} and G = X_t^T X_t
+enum YTerm { YT_NEG = 0, YT_COMP, YT_BNORM2, YT_BY, YT_YGY, YT_YMAX, YT_YNORM2, YT_DY2,
+             YT_CHANGED, YT_NOTCONV };
+// X-half terms, for the iterate (X_{t+1}, Y_{t+1}) leaving a sweep:
+//   graX_i = H x_i - P_i with H = Y Y^T and P = M Y^T
+enum XTerm { XT_NEG = 0, XT_COMP, XT_PNORM2, XT_XMAX, XT_XNORM2, XT_DX2, XT_XP,
+             XT_CHANGED, XT_NOTCONV, XT_VALID };
+// statistics record of iterate t
+enum Stat { ST_ITER = 0, ST_F, ST_EABS, ST_REL, ST_STEP, ST_NEG, ST_COMP, ST_SG, ST_XYMAX,
+            ST_CHANGED_COLS, ST_CHANGED_ROWS, ST_NOTCONV, ST_FP64, ST_MSQ, ST_VALID };
+
+// Device-resident control block of one problem.
+struct DevState {
+  int iter;          // index t of the current iterate (buffers t & 1)
+  int done;          // set by the finalize when a stopping test holds
+  unsigned err;      // ERR_* bits
+  unsigned xblocks_done;   // last-block counter of the X kernel
+  int stop_reason;   // 1 = rel-KKT target, 2 = step tolerance
+  int pad[3];
+  double stats[STAT_CAP][NSTAT];
+  double xiter[2][NXT];     // X-half terms of the iterate held in buffers 0 / 1
+  double msq;               // ||M||_F^2 of the resident window
+};
+
+// One problem as the kernels see it.
+struct Problem {
+  int n, m, k;            // rows, resident columns, rank
+  int ld;                 // leading dimension of M (elements, multiple of 32)
+  int mcap;               // ring capacity (columns)
+  int head;               // physical column of logical column 0
+  const void* M;          // ld x mcap, column-major, float or double
+  double* X[2];           // n x k row-major, FP64
+  float* X32[2];          // FP32 copy of X
+  double* Y[2];           // k x mcap column-major (physical column order), FP64
+  uint32_t* ymask[2];     // passive set of each column
+  uint32_t* xmask[2];     // passive set of each row
+  double* G;              // k x k, X^T X of the current iterate
+  const double* colsq;    // ||M_{:,j}||^2 per physical column
+  void* Ppart;            // [Q][ld][k] partial M Y^T (accumulate type)
+  double* Hpart;          // [Q][k][k]
+  double* Yterms;         // [Q][NYT]
+  double* Xpart;          // [nxblk][k*k + NXT]
+  DevState* st;
+  double kkt_target;      // <= 0 disables
+  double stol;            // <= 0 disables
+  int warm;               // 0 cold, 1 previous sweep (new columns are seeded at append)
+  int fp64_pass;          // 1 when this sweep's M pass runs in FP64
+};
+
+enum Mode { MODE_SWEEP = 0, MODE_PRIME = 1, MODE_KKT = 2 };
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after SPIN_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < SPIN_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 1-D bulk asynchronous copy global -> shared (the TMA engine), completion
+// counted in bytes on the mbarrier.  dst, src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Fused multiply-add in the precision of the operands (no implicit promotion).
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------
+// Warp reductions (fixed lane order => deterministic)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Reduce-scatter of V = 2^p <= 32 values held by every lane: afterwards lane l
+// holds the warp-wide sum of value (l & (V-1)).  V-1 + 5-p shuffles.
+template <int V, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[V]) {
+  static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = V / 2; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      T keep = upper ? v[i + o] : v[i];
+      T send = upper ? v[i] : v[i + o];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  T r = v[0];
+#pragma unroll
+  for (int o = V; o < 32; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+__device__ __forceinline__ int pow2ceil_int(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+__device__ __forceinline__ void set_err(DevState* st, unsigned bits) { atomicOr(&st->err, bits); }
+
+}  // namespace nmfgb

@@ -1,0 +1,327 @@
+// Warm-started Lawson-Hanson NNLS for one k-variable subproblem per thread
+// (problem "qp" of Sec. 2: min 1/2 y'Gy - b'y, y >= 0, with G = X^T X for a
+// column of Y or G = Y Y^T for a row of X).
+//
+// GB300 design notes.  FP64 on this part is slow (about 1/60 of FP32, a
+// dependent FMA takes tens of ns and a divide hundreds), so the solver never
+// refactors G from scratch per column.  It keeps A = inv(G_PP) for the
+// current passive set P and changes it by one-rank bordering / downdating
+// when a variable enters or leaves (one reciprocal and O(k^2) FMAs each) --
+// the paper's remark that the factorization of the previous solve can be
+// reused (Sec. 2).  A per-CTA cache holds inv(G_PP) for the passive sets of
+// sampled neighbouring columns, so that a column whose passive set did not
+// change costs two k x k mat-vecs: z = A b and w = b - G z.
+//
+// Decisions shared with the oracle (same readings, separate code):
+//   entering test w_i > tol, tol = 10 k eps (max|b| + max_i G_ii max|y|),
+//   lowest index first on ties, Schur pivot <= 1e-14 max_i G_ii blocks the
+//   variable, an entering variable whose first value is <= 0 is blocked,
+//   at most 5k + 10 outer iterations.
+#pragma once
+
+#include "nmf_common.cuh"
+
+namespace nmfgb {
+
+// 1/x in FP64 by Newton-Raphson refinement r <- r (2 - x r) of an FP32
+// reciprocal seed: the error squares each step (2^-23 -> 2^-46 -> rounding),
+// two FMAs per step instead of the long FP64 divide.  Arguments outside the
+// FP32 normal range fall back to the division.
+__device__ __forceinline__ double rcp64(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  double e = __fma_rn(-x, r, 1.0);
+  r = __fma_rn(r, e, r);
+  e = __fma_rn(-x, r, 1.0);
+  return __fma_rn(r, e, r);
+}
+
+// sum_c [c in P] a[c] * b[c] as a pairwise tree (dependency depth 1 + log2 K)
+template <int K>
+__device__ __forceinline__ double dot_masked(const double* a, const double (&b)[K], uint32_t P) {
+  double t[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) t[c] = ((P >> c) & 1u) ? a[c] * b[c] : 0.0;
+#pragma unroll
+  for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+    for (int c = 0; c + w < K; c += 2 * w) t[c] += t[c + w];
+  return t[0];
+}
+
+template <int K>
+struct InvCache {
+  int n;
+  uint32_t mask[CACHE_N];
+  double inv[CACHE_N][K * K];
+};
+
+template <int K>
+struct NnlsSolver {
+  const double* G;   // k x k row-major (shared memory)
+  double gmax;
+  double pivot_min;
+  double eps;
+
+  __device__ void init(const double* Gs, double eps_) {
+    G = Gs;
+    double g = 0.0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) g = fmax(g, Gs[a * K + a]);
+    gmax = g;
+    pivot_min = 1e-14 * g;
+    eps = eps_;
+  }
+
+  // A = inv(G_PP) -> inv(G_{P+i}); false (A unchanged) if the Schur pivot is
+  // not above pivot_min.
+  __device__ bool add(double* A, uint32_t P, int i) const {
+    double gi[K], u[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) gi[c] = G[c * K + i];
+#pragma unroll
+    for (int a = 0; a < K; ++a) u[a] = ((P >> a) & 1u) ? dot_masked<K>(A + a * K, gi, P) : 0.0;
+    const double s = G[i * K + i] - dot_masked<K>(G + i * K, u, P);
+    if (!(s > pivot_min)) return false;
+    const double rs = rcp64(s);
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (!((P >> a) & 1u)) continue;
+      const double ua = u[a] * rs;
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        if ((P >> c) & 1u) A[a * K + c] = fmad(ua, u[c], A[a * K + c]);
+      A[a * K + i] = -ua;
+      A[i * K + a] = -ua;
+    }
+    A[i * K + i] = rs;
+    return true;
+  }
+
+  // A = inv(G_PP) with i in P -> inv(G_{P-i}).
+  __device__ void remove(double* A, uint32_t P, int i) const {
+    const double rd = rcp64(A[i * K + i]);
+    double ci[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) ci[a] = (((P >> a) & 1u) && a != i) ? A[a * K + i] : 0.0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (!((P >> a) & 1u) || a == i) continue;
+      const double f = ci[a] * rd;
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        if (((P >> c) & 1u) && c != i) A[a * K + c] = fmad(-f, ci[c], A[a * K + c]);
+    }
+  }
+
+  // inv(G_PP) from scratch, variables added in ascending order; variables
+  // whose pivot fails are dropped from the returned mask and set in *blocked.
+  __device__ uint32_t build(double* A, uint32_t P, uint32_t* blocked) const {
+    uint32_t Q = 0;
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) {
+      if (!((P >> i) & 1u)) continue;
+      if (add(A, Q, i)) Q |= 1u << i;
+      else if (blocked) *blocked |= 1u << i;
+    }
+    return Q;
+  }
+
+  __device__ void apply(const double* A, uint32_t P, const double (&b)[K], double (&z)[K]) const {
+#pragma unroll
+    for (int a = 0; a < K; ++a) z[a] = ((P >> a) & 1u) ? dot_masked<K>(A + a * K, b, P) : 0.0;
+  }
+
+  // w = b - G y, returns the entering index (or -1) for the outer loop.
+  __device__ int entering(const double (&b)[K], const double (&y)[K], uint32_t P, uint32_t blocked,
+                          double bmax) const {
+    double ymax = 0.0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) ymax = fmax(ymax, y[a]);
+    const double tol = 10.0 * K * eps * (bmax + gmax * ymax);
+    int t = -1;
+    double best = tol;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const double w = b[a] - dot_masked<K>(G + a * K, y, 0xffffffffu);
+      const bool cand = !(((P | blocked) >> a) & 1u);
+      if (cand && w > best) {
+        best = w;
+        t = a;
+      }
+    }
+    return t;
+  }
+
+  // Inner loop of Lawson-Hanson from the feasible y (y_P > 0).  t_in is the
+  // variable that just entered (or -1 on a warm start).
+  __device__ void inner(double* A, const double (&b)[K], double (&y)[K], uint32_t& P,
+                        uint32_t& blocked, int t_in) const {
+    bool first = true;
+#pragma unroll 1
+    for (int it = 0; it <= K + 1; ++it) {
+      if (!P) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) y[a] = 0.0;
+        return;
+      }
+      double z[K];
+      apply(A, P, b, z);
+      if (first && t_in >= 0) {
+        double zt = 0.0;
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+          if (a == t_in) zt = z[a];
+        if (!(zt > 0.0)) {
+          remove(A, P, t_in);
+          P &= ~(1u << t_in);
+          blocked |= 1u << t_in;
+          return;
+        }
+      }
+      first = false;
+      bool feasible = true;
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if (((P >> a) & 1u) && !(z[a] > 0.0)) feasible = false;
+      if (feasible) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) y[a] = ((P >> a) & 1u) ? z[a] : 0.0;
+        return;
+      }
+      double alpha = 2.0;
+      int q = -1;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        if (!((P >> a) & 1u) || z[a] > 0.0) continue;
+        const double r = y[a] * rcp64(y[a] - z[a]);
+        if (r < alpha) {
+          alpha = r;
+          q = a;
+        }
+      }
+      if (q < 0) {   // only reachable through NaN: take the first infeasible one
+        alpha = 0.0;
+#pragma unroll
+        for (int a = K - 1; a >= 0; --a)
+          if (((P >> a) & 1u) && !(z[a] > 0.0)) q = a;
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if ((P >> a) & 1u) y[a] = fmad(alpha, z[a] - y[a], y[a]);
+      // drop q and every passive variable that reached zero
+      uint32_t drop = 1u << q;
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if (((P >> a) & 1u) && !(y[a] > 0.0)) drop |= 1u << a;
+#pragma unroll 1
+      for (int a = 0; a < K; ++a) {
+        if (!((drop >> a) & 1u)) continue;
+        remove(A, P, a);
+        P &= ~(1u << a);
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if ((drop >> a) & 1u) y[a] = 0.0;
+    }
+  }
+
+  // Full solve.  y holds the warm start on entry (>= 0; ignored when cold)
+  // and the solution on exit; A is per-thread scratch of K*K doubles.
+  // Returns 0 when converged, 1 at the iteration cap.  *mask_out gets the
+  // support of y.
+  __device__ int solve(double* A, const double (&b)[K], double (&y)[K], bool warm,
+                       const InvCache<K>* cache, uint32_t* mask_out) const {
+    uint32_t P = 0, blocked = 0;
+    double bmax = 0.0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      bmax = fmax(bmax, fabs(b[a]));
+      if (warm && y[a] > 0.0) P |= 1u << a;
+      else y[a] = 0.0;
+    }
+    int hit = -1;
+    if (P && cache) {
+      for (int e = 0; e < cache->n; ++e)
+        if (cache->mask[e] == P) {
+          hit = e;
+          break;
+        }
+    }
+    if (hit >= 0) {
+      // fast path: the passive set of the warm start is still optimal
+      const double* C = cache->inv[hit];
+      double z[K];
+      apply(C, P, b, z);
+      bool feasible = true;
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if (((P >> a) & 1u) && !(z[a] > 0.0)) feasible = false;
+      if (feasible && entering(b, z, P, 0u, bmax) < 0) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) y[a] = ((P >> a) & 1u) ? z[a] : 0.0;
+        *mask_out = P;
+        return 0;
+      }
+#pragma unroll
+      for (int e = 0; e < K * K; ++e) A[e] = C[e];
+    } else if (P) {
+      const uint32_t Q = build(A, P, &blocked);
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if (((P & ~Q) >> a) & 1u) y[a] = 0.0;
+      P = Q;
+    }
+    if (P) inner(A, b, y, P, blocked, -1);
+    int status = 1;
+#pragma unroll 1
+    for (int outer = 0; outer < 5 * K + 10; ++outer) {
+      const int t = entering(b, y, P, blocked, bmax);
+      if (t < 0) {
+        status = 0;
+        break;
+      }
+      if (!add(A, P, t)) {
+        blocked |= 1u << t;
+        continue;
+      }
+      P |= 1u << t;
+      inner(A, b, y, P, blocked, t);
+    }
+    uint32_t mask = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+      if (y[a] > 0.0) mask |= 1u << a;
+    *mask_out = mask;
+    return status;
+  }
+};
+
+// Build the per-CTA inverse cache from up to CACHE_N sampled passive sets
+// (called by every thread of the block; G must be in shared memory).
+template <int K>
+__device__ void build_cache(InvCache<K>* cache, const NnlsSolver<K>& S, const uint32_t* samples,
+                            int nsamples) {
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int s = 0; s < nsamples; ++s) {
+      const uint32_t msk = samples[s];
+      if (!msk) continue;
+      bool seen = false;
+      for (int e = 0; e < n; ++e) seen |= cache->mask[e] == msk;
+      if (!seen && n < CACHE_N) cache->mask[n++] = msk;
+    }
+    cache->n = n;
+  }
+  __syncthreads();
+  const int e = threadIdx.x;
+  if (e < cache->n) {
+    uint32_t blocked = 0;
+    const uint32_t Q = S.build(cache->inv[e], cache->mask[e], &blocked);
+    if (Q != cache->mask[e]) cache->mask[e] = 0xffffffffu;   // degenerate: never matches
+  }
+  __syncthreads();
+}
+
+}  // namespace nmfgb

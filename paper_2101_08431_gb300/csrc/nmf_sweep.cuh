@@ -1,0 +1,620 @@
+// The ANLS sweep on GB300 (Alg. "anls" of Sec. 2, Y-update first):
+//
+//   ypass  : one fused pass over M.  A cluster of C CTAs owns a contiguous
+//            range of time columns; CTA c of the cluster owns rows
+//            [c R, (c+1) R).  Column tiles of TJ columns are staged into
+//            shared memory by the bulk-copy (TMA) engine through an S-deep
+//            mbarrier ring.  Per tile: B = X^T M_tile (thread-owned rows,
+//            reduce-scatter in the warp, fixed-order sums across warps and,
+//            through distributed shared memory, across the cluster), one FP64
+//            warm-started NNLS per column (problem "qp" with C = X), then
+//            P += M_tile Y_tile^T and H += Y_tile Y_tile^T from the same
+//            staged tile -- M is read from HBM exactly once per sweep.  The
+//            same pass produces the Y-half KKT terms of the incoming iterate
+//            (graY = G y - b, eq. "eqn:kkt").
+//   xpass  : one thread per row of X: sums the P partials (fixed order),
+//            solves the row NNLS (problem "qp" with C = Y^T), and the last
+//            block to finish forms G = X^T X for the next sweep together with
+//            the objective and KKT error of the iterate from the Grams
+//            (Sec. 5.1), with no second read of M.
+#pragma once
+
+#include "nmf_nnls.cuh"
+
+namespace nmfgb {
+
+// Compile-time tile shape of the M pass.
+template <typename TM, typename TA, int K>
+struct YTraits {
+  static constexpr bool FP64A = sizeof(TA) == 8;
+  static constexpr int T = 512;
+  static constexpr int RPT = FP64A ? (K <= 8 ? 2 : 1) : (K <= 4 ? 6 : (K <= 8 ? 4 : 2));
+  static constexpr int TJ = FP64A ? (K <= 4 ? 4 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 8 : (K <= 8 ? 4 : 2));
+  static constexpr int V = TJ * K;
+  static constexpr int VP = (V <= 1) ? 1 : (V <= 2) ? 2 : (V <= 4) ? 4 : (V <= 8) ? 8 : (V <= 16) ? 16 : 32;
+  static_assert(V <= 32, "B tile must fit one warp reduce-scatter");
+};
+
+__host__ __device__ inline int wrap_col(int head, int j, int mcap) {
+  int p = head + j;
+  return p >= mcap ? p - mcap : p;
+}
+
+// Shared-memory layout of the M pass (dynamic smem, 128-byte aligned parts).
+template <typename TM, typename TA, int K>
+struct YSmem {
+  using Tr = YTraits<TM, TA, K>;
+  static constexpr int NW = Tr::T / 32;
+  struct Small {
+    uint64_t full[8];                  // stage barriers (S <= 8)
+    double G[K * K];
+    double Hacc[K * K];
+    double Bfull[Tr::VP];
+    double Bpart[Tr::VP];
+    double red[NW][Tr::VP];
+    double xch[2][8][Tr::VP];          // cluster exchange slots (C <= 8)
+    double ybufD[Tr::TJ][K];
+    TA ybufA[Tr::TJ][K];
+    uint32_t samples[CACHE_N];
+    double yt[Tr::TJ][NYT];            // per-column-thread KKT / objective terms
+    InvCache<K> cache;
+  };
+  static constexpr size_t SMALL_BYTES = (sizeof(Small) + 127) & ~size_t(127);
+  __host__ __device__ static constexpr size_t small_bytes() { return SMALL_BYTES; }
+  __host__ __device__ static size_t stage_bytes(int R) { return size_t(Tr::TJ) * R * sizeof(TM); }
+};
+
+template <typename TM, typename TA, int K>
+__global__ void __launch_bounds__(512, 1)
+    ypass_kernel(Problem p, int mode, int S, int C, int R, int Q) {
+  using Tr = YTraits<TM, TA, K>;
+  using Sm = YSmem<TM, TA, K>;
+  constexpr int T = Tr::T, RPT = Tr::RPT, TJ = Tr::TJ, VP = Tr::VP;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  typename Sm::Small& sm = *reinterpret_cast<typename Sm::Small*>(smem_raw);
+  TM* stages = reinterpret_cast<TM*>(smem_raw + Sm::small_bytes());
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int q = blockIdx.x / C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  DevState* st = p.st;
+  if (st->done) return;                       // uniform: written by an earlier launch
+  const int cur = st->iter & 1, nxt = cur ^ 1;
+
+  const int c0 = (int)(((long long)q * p.m) / Q);
+  const int c1 = (int)(((long long)(q + 1) * p.m) / Q);
+  const int ncols = c1 - c0;
+  const int ntiles = (ncols + TJ - 1) / TJ;
+  const int r0 = crank * R;
+  const int rows_c = max(0, min(R, p.ld - r0));
+  const TM* M = static_cast<const TM*>(p.M);
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int t, int s) {
+    const int tj = min(TJ, ncols - t * TJ);
+    const uint32_t bytes = (uint32_t)rows_c * (uint32_t)sizeof(TM);
+    mbar_arrive_expect_tx(&sm.full[s], bytes * (uint32_t)tj);
+    if (bytes) {
+      TM* dst = stages + (size_t)s * TJ * R;
+      for (int jj = 0; jj < tj; ++jj) {
+        const int phys = wrap_col(p.head, c0 + t * TJ + jj, p.mcap);
+        bulk_g2s(dst + (size_t)jj * R, M + (size_t)phys * p.ld + r0, bytes, &sm.full[s]);
+      }
+    }
+  };
+  if (tid == 0)
+    for (int t = 0; t < min(S, ntiles); ++t) issue(t, t);
+
+  // G, the rows of X owned by this thread, accumulators
+  if (tid < K * K) {
+    sm.G[tid] = p.G[tid];
+    sm.Hacc[tid] = 0.0;
+  }
+  TA xr[RPT][K];
+  TA pacc[RPT][K];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int row = r0 + tid + r * T;
+    const bool ok = (tid + r * T) < rows_c && row < p.n;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      TA v = TA(0);
+      if (ok) {
+        if (Tr::FP64A) v = (TA)p.X[cur][(size_t)row * K + a];
+        else v = (TA)p.X32[cur][(size_t)row * K + a];
+      }
+      xr[r][a] = v;
+      pacc[r][a] = TA(0);
+    }
+  }
+  // passive sets of sampled columns of this cluster -> inverse cache
+  if (tid < CACHE_N) {
+    uint32_t msk = 0;
+    if (mode == MODE_SWEEP && p.warm && ncols > 0) {
+      const int j = c0 + (int)(((long long)tid * ncols) / CACHE_N);
+      msk = p.ymask[cur][wrap_col(p.head, j, p.mcap)];
+    }
+    sm.samples[tid] = msk;
+  }
+  __syncthreads();
+  NnlsSolver<K> solver;
+  solver.init(sm.G, Tr::FP64A ? 2.220446049250313e-16 : 1.1920928955078125e-07);
+  if (mode == MODE_SWEEP) build_cache<K>(&sm.cache, solver, sm.samples, CACHE_N);
+  else if (tid == 0) sm.cache.n = 0;
+
+  if (tid < TJ)
+    for (int e = 0; e < NYT; ++e) sm.yt[tid][e] = 0.0;
+  double Ascr[K * K];
+  bool timed_out = false;
+
+  for (int t = 0; t < ntiles; ++t) {
+    const int s = t % S;
+    const uint32_t parity = (uint32_t)((t / S) & 1);
+    const int tj = min(TJ, ncols - t * TJ);
+    // the column threads fetch their warm start before the contraction, so
+    // the load latency hides behind it
+    double yo[K];
+    uint32_t old_mask = 0;
+    int phys = 0;
+    if (tid < tj) {
+      phys = wrap_col(p.head, c0 + t * TJ + tid, p.mcap);
+#pragma unroll
+      for (int a = 0; a < K; ++a) yo[a] = p.Y[cur][(size_t)phys * K + a];
+      old_mask = p.ymask[cur][phys];
+    }
+    if (!mbar_wait(&sm.full[s], parity)) timed_out = true;
+    const TM* tile = stages + (size_t)s * TJ * R;
+
+    // ---- B partial = X_rows^T M_tile over this thread's rows
+    TA acc[VP];
+#pragma unroll
+    for (int e = 0; e < VP; ++e) acc[e] = TA(0);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int rr = tid + r * T;
+      if (rr < rows_c) {
+#pragma unroll
+        for (int jj = 0; jj < TJ; ++jj) {
+          const TA mv = (TA)tile[(size_t)jj * R + rr];
+#pragma unroll
+          for (int a = 0; a < K; ++a) acc[jj * K + a] = fmad(mv, xr[r][a], acc[jj * K + a]);
+        }
+      }
+    }
+    {
+      const TA wsum = warp_reduce_scatter<VP, TA>(acc);
+      if (lane < VP) sm.red[warp][lane] = (double)wsum;
+    }
+    __syncthreads();
+    const int slot = t & 1;
+    if (tid < ((4 * VP + 31) & ~31)) {   // whole warps take part in the shuffles
+      // value tid/4: lane quad g adds warps g, g+4, ... then a quad tree
+      // (short FP64 chains, fixed order)
+      const int v = tid >> 2, g = tid & 3;
+      double bs = 0.0;
+      if (v < VP) {
+#pragma unroll
+        for (int w = g; w < Sm::NW; w += 4) bs += sm.red[w][v];
+      }
+      bs += __shfl_xor_sync(0xffffffffu, bs, 1);
+      bs += __shfl_xor_sync(0xffffffffu, bs, 2);
+      if (g == 0 && v < VP) sm.Bpart[v] = bs;
+    }
+    __syncthreads();
+    if (tid < VP) {
+      const double bs = sm.Bpart[tid];
+      if (C > 1) {
+        for (int rk = 0; rk < C; ++rk) {
+          double* dst = cluster.map_shared_rank(&sm.xch[slot][crank][tid], rk);
+          *dst = bs;
+        }
+      } else {
+        sm.Bfull[tid] = bs;
+      }
+    }
+    if (C > 1) {
+      cluster.sync();
+      if (tid < VP) {
+        double bs = 0.0;
+        for (int c = 0; c < C; ++c) bs += sm.xch[slot][c][tid];
+        sm.Bfull[tid] = bs;
+      }
+    }
+    __syncthreads();
+
+    // ---- one NNLS per column (threads 0..tj-1 of warp 0)
+    if (tid < TJ) {
+      double yn[K];
+#pragma unroll
+      for (int a = 0; a < K; ++a) yn[a] = 0.0;
+      if (tid < tj) {
+        double b[K];
+#pragma unroll
+        for (int a = 0; a < K; ++a) b[a] = sm.Bfull[tid * K + a];
+        if (mode != MODE_PRIME) {
+          // Y-half KKT terms of the incoming iterate: g = G y - b
+          double bn = 0.0, by = 0.0, ygy = 0.0, ymax = 0.0, yn2 = 0.0, neg = 0.0, comp = 0.0;
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+            const double g = dot_masked<K>(sm.G + a * K, yo, 0xffffffffu) - b[a];
+            const double mn = fmin(g, 0.0), pos = fmax(g, 0.0) * yo[a];
+            neg = fmad(mn, mn, neg);
+            comp = fmad(pos, pos, comp);
+            bn = fmad(b[a], b[a], bn);
+            by = fmad(b[a], yo[a], by);
+            ygy = fmad(yo[a], g + b[a], ygy);
+            ymax = fmax(ymax, yo[a]);
+            yn2 = fmad(yo[a], yo[a], yn2);
+            if (!isfinite(b[a])) set_err(st, ERR_NONFINITE);
+          }
+          double* yt = sm.yt[tid];
+          yt[YT_NEG] += neg;
+          yt[YT_COMP] += comp;
+          yt[YT_BNORM2] += bn;
+          yt[YT_BY] += by;
+          yt[YT_YGY] += ygy;
+          yt[YT_YMAX] = fmax(yt[YT_YMAX], ymax);
+          yt[YT_YNORM2] += yn2;
+        }
+        if (mode == MODE_SWEEP) {
+#pragma unroll
+          for (int a = 0; a < K; ++a) yn[a] = yo[a];
+          uint32_t msk = 0;
+          const int stt = solver.solve(Ascr, b, yn, p.warm != 0, &sm.cache, &msk);
+          double d2 = 0.0;
+#pragma unroll
+          for (int a = 0; a < K; ++a) d2 = fmad(yn[a] - yo[a], yn[a] - yo[a], d2);
+          double* yt = sm.yt[tid];
+          yt[YT_DY2] += d2;
+          yt[YT_CHANGED] += (old_mask != msk) ? 1.0 : 0.0;
+          yt[YT_NOTCONV] += (double)stt;
+          if (crank == 0) {
+#pragma unroll
+            for (int a = 0; a < K; ++a) p.Y[nxt][(size_t)phys * K + a] = yn[a];
+            p.ymask[nxt][phys] = msk;
+          }
+        } else {
+          uint32_t msk = 0;
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+            yn[a] = yo[a];
+            if (yo[a] > 0.0) msk |= 1u << a;
+          }
+          if (mode == MODE_PRIME && crank == 0) p.ymask[cur][phys] = msk;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        sm.ybufD[tid][a] = yn[a];
+        sm.ybufA[tid][a] = (TA)yn[a];
+      }
+    }
+    __syncthreads();
+
+    // ---- P += M_tile Y_tile^T (own rows), H += Y_tile Y_tile^T
+    if (mode != MODE_KKT) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int rr = tid + r * T;
+        if (rr < rows_c) {
+#pragma unroll
+          for (int jj = 0; jj < TJ; ++jj) {
+            if (jj < tj) {
+              const TA mv = (TA)tile[(size_t)jj * R + rr];
+#pragma unroll
+              for (int a = 0; a < K; ++a) pacc[r][a] = fmad(mv, sm.ybufA[jj][a], pacc[r][a]);
+            }
+          }
+        }
+      }
+      if (tid >= 32 && tid < 32 + K * K) {     // H += sum_jj y_jj y_jj^T as a pairwise tree
+        const int e = tid - 32, a = e / K, c = e % K;
+        double hp[TJ];
+#pragma unroll
+        for (int jj = 0; jj < TJ; ++jj) hp[jj] = jj < tj ? sm.ybufD[jj][a] * sm.ybufD[jj][c] : 0.0;
+#pragma unroll
+        for (int w = 1; w < TJ; w <<= 1)
+#pragma unroll
+          for (int jj = 0; jj + w < TJ; jj += 2 * w) hp[jj] += hp[jj + w];
+        sm.Hacc[e] += hp[0];
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && t + S < ntiles) issue(t + S, s);
+  }
+  if (timed_out) set_err(st, ERR_TIMEOUT);
+
+  // ---- epilogue: partials of this cluster
+  TA* Pp = static_cast<TA*>(p.Ppart);
+  if (mode != MODE_KKT) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int rr = tid + r * T;
+      const int row = r0 + rr;
+      if (rr < rows_c && row < p.n) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) Pp[((size_t)q * p.ld + row) * K + a] = pacc[r][a];
+      }
+    }
+  }
+  if (crank == 0) {
+    if (tid < K * K) p.Hpart[(size_t)q * K * K + tid] = (mode == MODE_KKT) ? 0.0 : sm.Hacc[tid];
+    if (tid < NYT) {   // fixed-order combine of the column threads' terms
+      double v = sm.yt[0][tid];
+      for (int jj = 1; jj < TJ; ++jj) v = (tid == YT_YMAX) ? fmax(v, sm.yt[jj][tid]) : v + sm.yt[jj][tid];
+      p.Yterms[(size_t)q * NYT + tid] = v;
+    }
+  }
+  if (C > 1) cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Combine the terms of iterate t into its statistics record (Sec. 5.1 KKT
+// error with r = max(graX, 0), s = max(graY, 0), 2-norms; f from the Grams).
+// ---------------------------------------------------------------------------
+__device__ inline void combine_stats(const double* yterm, const double* xterm, double msq,
+                                     double dx2, int iter, int fp64, double* out) {
+  const double neg = yterm[YT_NEG] + xterm[XT_NEG];
+  const double comp = yterm[YT_COMP] + xterm[XT_COMP];
+  const double sg = sqrt(xterm[XT_PNORM2]) + sqrt(yterm[YT_BNORM2]);
+  const double xymax = fmax(xterm[XT_XMAX], yterm[YT_YMAX]);
+  const double e1 = sqrt(neg), e2 = sqrt(comp);
+  const double r1 = sg > 0.0 ? e1 / sg : e1;
+  const double d2 = sg * xymax;
+  const double r2 = d2 > 0.0 ? e2 / d2 : e2;
+  for (int e = 0; e < NSTAT; ++e) out[e] = 0.0;
+  out[ST_ITER] = iter;
+  out[ST_F] = 0.5 * (msq - 2.0 * yterm[YT_BY] + yterm[YT_YGY]);
+  out[ST_EABS] = fmax(e1, e2);
+  out[ST_REL] = fmax(r1, r2);
+  out[ST_STEP] = (dx2 >= 0.0)
+                     ? sqrt(dx2 + yterm[YT_DY2]) / (1.0 + sqrt(xterm[XT_XNORM2] + yterm[YT_YNORM2]))
+                     : -1.0;
+  out[ST_NEG] = e1;
+  out[ST_COMP] = e2;
+  out[ST_SG] = sg;
+  out[ST_XYMAX] = xymax;
+  out[ST_CHANGED_COLS] = yterm[YT_CHANGED];
+  out[ST_NOTCONV] = yterm[YT_NOTCONV];
+  out[ST_FP64] = fp64;
+  out[ST_MSQ] = msq;
+  out[ST_VALID] = xterm[XT_VALID];
+}
+
+template <int K>
+struct XTraits {
+  static constexpr int NW = K >= 16 ? 4 : 8;   // warps (static smem bound at k = 16)
+  static constexpr int T = NW * 32;
+  static constexpr int RB = 32;          // rows per block (lane <-> row)
+  static constexpr int NV = K * K + NXT; // Gram partial + X-half terms
+  static constexpr int NVC = (NV + 31) / 32;
+};
+
+// Sum over p of src[p * stride + e] for e < nval, in a fixed order, with
+// short FP64 dependency chains: 8 threads per value each add every 8th term,
+// then a 3-level shuffle tree inside the 8-lane group.  Called by all T
+// threads of the block; writes out[e] (shared memory).  max_e: 1 = max.
+template <int T>
+__device__ void tree_sum(const double* src, int nparts, size_t stride, int nval, double* out,
+                         int max_e) {
+  constexpr int G = 8, VPB = T / G, U = 8;   // U loads in flight per thread
+  const int g = threadIdx.x & (G - 1), vi = threadIdx.x / G;
+  for (int e0 = 0; e0 < nval; e0 += VPB) {
+    const int e = e0 + vi;
+    const bool ok = e < nval;
+    const bool is_max = ok && e == max_e;
+    double r = 0.0;
+    for (int q0 = g; q0 < nparts; q0 += G * U) {
+      double w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * G;
+        w[u] = (ok && q < nparts) ? src[(size_t)q * stride + e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) r = is_max ? fmax(r, w[u]) : r + w[u];
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, r, o);
+      r = is_max ? fmax(r, w) : r + w;
+    }
+    if (ok && g == 0) out[e] = r;
+  }
+}
+
+// Row pass: rows [32 b, 32 b + 32) of X.  The 8 warps split the cluster
+// partials of P = M Y^T (lane <-> row, accumulated in the pass's precision),
+// warp 0 solves the 32 row NNLS problems and forms the X-half terms and the
+// Gram partial; the last block to finish combines the blocks.
+template <typename TA, int K>
+__global__ void __launch_bounds__(XTraits<K>::T)
+    xpass_kernel(Problem p, int mode, int Q, int nxblk, double* kkt_out) {
+  using Tr = XTraits<K>;
+  constexpr int T = Tr::T, NW = Tr::NW, RB = Tr::RB, NV = Tr::NV;
+  __shared__ double H[K * K];
+  __shared__ TA psum[NW][RB][K];
+  __shared__ double fin[NV];
+  __shared__ double yfin[NYT];
+  __shared__ uint32_t samples[CACHE_N];
+  __shared__ InvCache<K> cache;
+  __shared__ unsigned ticket;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  DevState* st = p.st;
+  if (st->done) return;
+  const int iter = st->iter;
+  const int cur = iter & 1, nxt = cur ^ 1;
+  const int row0 = blockIdx.x * RB;
+  const int row = row0 + lane;
+  const bool active = row < p.n;
+
+  tree_sum<T>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
+  if (tid < CACHE_N) {
+    uint32_t msk = 0;
+    if (mode == MODE_SWEEP && p.warm) {
+      const int nb = min(RB, p.n - row0);
+      msk = p.xmask[cur][row0 + (tid * nb) / CACHE_N];
+    }
+    samples[tid] = msk;
+  }
+  {
+    const TA* Pp = static_cast<const TA*>(p.Ppart);
+    TA acc[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) acc[a] = TA(0);
+    if (active)
+      for (int q0 = warp; q0 < Q; q0 += NW * 4) {   // four partials in flight per thread
+        TA w[4][K];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int qq = q0 + u * NW;
+#pragma unroll
+          for (int a = 0; a < K; ++a) w[u][a] = qq < Q ? Pp[((size_t)qq * p.ld + row) * K + a] : TA(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int a = 0; a < K; ++a) acc[a] += w[u][a];
+      }
+#pragma unroll
+    for (int a = 0; a < K; ++a) psum[warp][lane][a] = acc[a];
+  }
+  __syncthreads();
+  NnlsSolver<K> solver;
+  solver.init(H, 2.220446049250313e-16);
+  if (mode == MODE_SWEEP) build_cache<K>(&cache, solver, samples, CACHE_N);
+
+  if (warp == 0) {
+    double v[Tr::NVC * 32];
+#pragma unroll
+    for (int e = 0; e < Tr::NVC * 32; ++e) v[e] = 0.0;
+    if (active) {
+      double pr[K], xo[K], xn[K];
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += (double)psum[w][lane][a];
+        pr[a] = t;
+        xo[a] = p.X[cur][(size_t)row * K + a];
+        xn[a] = xo[a];
+      }
+      uint32_t msk = 0;
+      int stt = 0;
+      if (mode == MODE_SWEEP) {
+        double Ascr[K * K];
+        stt = solver.solve(Ascr, pr, xn, p.warm != 0, &cache, &msk);
+      } else {
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+          if (xo[a] > 0.0) msk |= 1u << a;
+      }
+      // X-half KKT terms of the iterate leaving this sweep: graX = H x - P
+      double neg = 0.0, comp = 0.0, pn = 0.0, xmax = 0.0, xn2 = 0.0, dx2 = 0.0, xp = 0.0;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        double g = -pr[a];
+#pragma unroll
+        for (int c = 0; c < K; ++c) g = fmad(H[a * K + c], xn[c], g);
+        const double mn = fmin(g, 0.0), pos = fmax(g, 0.0) * xn[a];
+        neg = fmad(mn, mn, neg);
+        comp = fmad(pos, pos, comp);
+        pn = fmad(pr[a], pr[a], pn);
+        xmax = fmax(xmax, xn[a]);
+        xn2 = fmad(xn[a], xn[a], xn2);
+        dx2 = fmad(xn[a] - xo[a], xn[a] - xo[a], dx2);
+        xp = fmad(xn[a], pr[a], xp);
+        if (!isfinite(pr[a])) set_err(st, ERR_NONFINITE);
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[a * K + c] = xn[a] * xn[c];
+      v[K * K + XT_NEG] = neg;
+      v[K * K + XT_COMP] = comp;
+      v[K * K + XT_PNORM2] = pn;
+      v[K * K + XT_XMAX] = xmax;
+      v[K * K + XT_XNORM2] = xn2;
+      v[K * K + XT_DX2] = dx2;
+      v[K * K + XT_XP] = xp;
+      v[K * K + XT_CHANGED] = (mode == MODE_SWEEP && p.xmask[cur][row] != msk) ? 1.0 : 0.0;
+      v[K * K + XT_NOTCONV] = (double)stt;
+      if (mode == MODE_SWEEP) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          p.X[nxt][(size_t)row * K + a] = xn[a];
+          p.X32[nxt][(size_t)row * K + a] = (float)xn[a];
+        }
+        p.xmask[nxt][row] = msk;
+      } else {
+#pragma unroll
+        for (int a = 0; a < K; ++a) p.X32[cur][(size_t)row * K + a] = (float)xo[a];
+        p.xmask[cur][row] = msk;
+      }
+    }
+    // block partial: max for XT_XMAX, sums for the rest (fixed lane order)
+    {
+      const double mx = warp_max(v[K * K + XT_XMAX]);
+      v[K * K + XT_XMAX] = 0.0;
+#pragma unroll
+      for (int c = 0; c < Tr::NVC; ++c) {
+        double chunk[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
+        const double r = warp_reduce_scatter<32, double>(chunk);
+        const int e = c * 32 + lane;
+        if (e < NV) p.Xpart[(size_t)blockIdx.x * NV + e] = (e == K * K + XT_XMAX) ? mx : r;
+      }
+    }
+  }
+  // last block to finish: G for the next sweep, terms and statistics
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(&st->xblocks_done, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(nxblk - 1)) return;
+  __threadfence();
+  tree_sum<T>(p.Xpart, nxblk, NV, NV, fin, K * K + XT_XMAX);
+  tree_sum<T>(p.Yterms, Q, NYT, NYT, yfin, YT_YMAX);
+  __syncthreads();
+  if (tid < K * K) p.G[tid] = fin[tid];
+  if (tid == 0) {
+    double xt[NXT];
+    for (int e = 0; e < NXT; ++e) xt[e] = fin[K * K + e];
+    xt[XT_VALID] = 1.0;
+    if (mode == MODE_PRIME) {
+      for (int e = 0; e < NXT; ++e) st->xiter[cur][e] = xt[e];
+    } else {
+      // statistics of iterate t: Y half from this sweep's M pass, X half from
+      // the sweep that produced X_t
+      double rec[NSTAT];
+      combine_stats(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
+      rec[ST_CHANGED_ROWS] = fin[K * K + XT_CHANGED];
+      rec[ST_NOTCONV] += fin[K * K + XT_NOTCONV];
+      for (int e = 0; e < NSTAT; ++e) st->stats[iter % STAT_CAP][e] = rec[e];
+      for (int e = 0; e < NXT; ++e) st->xiter[nxt][e] = xt[e];
+      const bool kkt_ok = p.kkt_target > 0.0 && rec[ST_VALID] > 0.0 && rec[ST_REL] <= p.kkt_target;
+      const bool step_ok = p.stol > 0.0 && rec[ST_STEP] >= 0.0 && rec[ST_STEP] <= p.stol;
+      if (kkt_ok) {
+        st->done = 1;
+        st->stop_reason = 1;
+      } else {
+        st->iter = iter + 1;
+        if (step_ok) {
+          st->done = 1;
+          st->stop_reason = 2;
+        }
+      }
+    }
+    st->xblocks_done = 0;
+    __threadfence();
+  }
+}
+
+}  // namespace nmfgb

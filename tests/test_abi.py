@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/nmf.h declares.  No compute call is made (no GPU here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nmf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nmf_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2101_08431_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2101_08431_gb300 import _native
+    names = _declared()
+    assert names, "no declarations parsed"
+    assert set(names) == set(_native.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_host_only_entry_points(lib):
+    from paper_2101_08431_gb300 import _native
+    cfg = _native.nmf_config()
+    lib.nmf_config_init(C.byref(cfg))
+    assert cfg.kkt_target == 1e-8 and cfg.prec == _native.NMF_PREC_MIXED and cfg.warm_start == 1
+    for s in range(9):
+        assert lib.nmf_status_string(s).decode()
+    assert lib.nmf_last_error(None) == b""
+    assert lib.nmf_launch_count(None) == 0
+
+
+def test_invalid_arguments_rejected_before_any_device_work(lib):
+    from paper_2101_08431_gb300 import _native
+    cfg = _native.nmf_config()
+    lib.nmf_config_init(C.byref(cfg))
+    h = C.c_void_p()
+    for n, k, mcap in ((0, 4, 10), (100, 0, 10), (100, 9, 10), (100, 17, 10), (100, 4, 0)):
+        cfg.n, cfg.k, cfg.m_capacity = n, k, mcap
+        assert lib.nmf_create(C.byref(cfg), C.byref(h)) == _native.NMF_EINVAL
+    assert lib.nmf_destroy(None) == _native.NMF_OK
+
+
+def test_library_is_built_for_sm_103a_only():
+    from paper_2101_08431_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
