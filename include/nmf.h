@@ -181,6 +181,39 @@ nmf_status nmf_set_timing(nmf_handle *h, int32_t on);
 nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launches,
                           double *xpass_ms, int64_t *xpass_launches);
 
+/* One ANLS sweep that allocates no memory at all.
+ *
+ * The paper has no counterpart: this is a deployment variant of nmf_sweep for
+ * callers that cannot allocate device memory where they run the sweep -- a
+ * latency-critical loop that must never block on cudaMalloc (which can
+ * synchronise the device and take milliseconds), a plug-in whose host
+ * framework has reserved all device memory for its own pool, or code that
+ * is allowed to allocate only during start-up.  It needs no handle and calls
+ * no allocating routine.
+ *
+ *   M          device, n x m FP32, column-major, leading dimension ldm equal to
+ *              n rounded up to a multiple of 32; rows n..ldm-1 must hold finite
+ *              values (zeros, say);
+ *   X, Y       device FP64: X n x k row-major, Y k x m column-major; on entry the
+ *              iterate (entries >= 0), on exit the next iterate: one sweep,
+ *              Y-update then X-update, with the FP64-accumulated M pass;
+ *   stats_dev  NULL or a device buffer of 16 doubles that receives the record of
+ *              the incoming iterate (index 1: f, 2: KKT error, 3: relative KKT);
+ *   cuda_stream  the stream the work is ordered on (NULL: the default stream);
+ *              the call returns once the work is enqueued.
+ * Limits: n <= 2048, m <= 4096, 1 <= k <= 8; larger sizes return NMF_ECAPACITY,
+ * a wrong ldm or a NULL pointer NMF_EINVAL.
+ * Working memory: one 5 MiB __device__ array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  All calls
+ * share it and it keeps the last call's contents (each call re-initialises what
+ * must start at zero), so calls whose work overlaps on the GPU -- on different
+ * streams or from different threads -- race on it; serialise them.
+ * Set-up: the first call on each device looks up the array's device address
+ * with that device current; make that first call before any stream capture
+ * on the device. */
+nmf_status nmf_sweep_noalloc(const float *M, int64_t n, int64_t m, int64_t ldm, int32_t k,
+                             double *X, double *Y, double *stats_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

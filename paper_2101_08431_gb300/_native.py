@@ -22,7 +22,7 @@ NMF_WARM_COLD, NMF_WARM_PREV = 0, 1
 EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns", "nmf_num_columns",
            "nmf_set_factors", "nmf_get_factors", "nmf_sweep", "nmf_set_pass_mode",
            "nmf_objective_kkt", "nmf_status_string", "nmf_last_error", "nmf_launch_count",
-           "nmf_set_timing", "nmf_get_timing")
+           "nmf_set_timing", "nmf_get_timing", "nmf_sweep_noalloc")
 
 
 class nmf_config(C.Structure):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH):
     L.nmf_set_timing.argtypes = [H, C.c_int32]
     L.nmf_get_timing.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.nmf_sweep_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     for name in EXPORTS:
         if name not in ("nmf_config_init", "nmf_num_columns", "nmf_status_string", "nmf_last_error",
                         "nmf_launch_count"):
