@@ -59,8 +59,9 @@ typedef enum {
 
 typedef enum {
     NMF_PREC_FP64 = 0,   /* M stored and contracted in FP64                  */
-    NMF_PREC_MIXED = 1   /* M stored FP32; FP32 passes, then FP64-accumulated
-                            refinement passes; NNLS, Grams and KKT in FP64   */
+    NMF_PREC_MIXED = 1   /* M stored FP32; FP32 passes, then compensated
+                            (double-float) refinement passes; NNLS, Grams
+                            and KKT in FP64                                  */
 } nmf_precision;
 
 enum { NMF_DTYPE_F64 = 0, NMF_DTYPE_F32 = 1 };
@@ -149,8 +150,10 @@ nmf_status nmf_sweep(nmf_handle *h, int32_t nsweeps, nmf_stats *stats);
 
 /* NMF_PREC_MIXED handles: force the arithmetic of the following M passes
  * (0 = FP32 contraction, 1 = FP64-accumulated contraction of the FP32 M,
- * -1 = automatic: FP32 until the relative KKT error reaches mixed_switch or
- * stalls, then FP64-accumulated).  NMF_PREC_FP64 handles ignore it. */
+ * 2 = compensated FP32 (double-float) contraction of the FP32 M, about 44
+ * significant bits; -1 = automatic: FP32 until the relative KKT error reaches
+ * mixed_switch or stalls, then compensated).  NMF_PREC_FP64 handles ignore it.
+ * NMF_EINVAL for any other mode. */
 nmf_status nmf_set_pass_mode(nmf_handle *h, int32_t mode);
 
 /* Objective and KKT error of the current iterate from one read-only,

@@ -145,6 +145,8 @@ struct nmf_handle {
   uint32_t* dYm[2] = {nullptr, nullptr};
   uint32_t* dXm[2] = {nullptr, nullptr};
   double* dG = nullptr;
+  double* dGtab = nullptr;
+  int* dGok = nullptr;
   double* dColsq = nullptr;
   void* dPpart = nullptr;
   double* dHpart = nullptr;
@@ -171,7 +173,7 @@ struct nmf_handle {
   int64_t launches = 0;
   std::string last_error;
   KernelSet ks[NVAR]{};
-  bool has[NVAR] = {false, false, false};
+  bool has[NVAR] = {false, false, false, false};
   int max_clusters[NVAR][4] = {};   // per variant, cluster size 1, 2, 4, 8 (full smem)
   // per-kernel timing (event triplets around each sweep's two launches)
   bool timing = false;
@@ -201,7 +203,7 @@ nmf_status fail(nmf_handle* h, nmf_status s, const std::string& msg) {
 
 bool make_plan(const nmf_handle* h, int var, YPlan* L) {
   const KernelSet& K = h->ks[var];
-  const int rmax = K.RPT * 512;
+  const int rmax = K.rows;
   int C = 1, R = 0;
   for (C = 1; C <= 8; C <<= 1) {
     R = round_up((h->ld + C - 1) / C, 32);
@@ -215,7 +217,9 @@ bool make_plan(const nmf_handle* h, int var, YPlan* L) {
   long long S = ((long long)h->smem_optin - (long long)K.small_bytes) / (long long)stage;
   if (S > 8) S = 8;
   if (S > ntiles) S = ntiles;
-  if (S < 1) return false;
+  // the pipeline refills the stage of tile t-1 while tile t is staged: two
+  // stages at least whenever there is more than one tile
+  if (S < (ntiles > 1 ? 2 : 1)) return false;
   const size_t smem = K.small_bytes + (size_t)S * stage;
   // persistent grid: never more clusters than the device holds at once
   const int ci = C == 1 ? 0 : (C == 2 ? 1 : (C == 4 ? 2 : 3));
@@ -250,6 +254,8 @@ Problem make_problem(const nmf_handle* h, int var) {
     p.xmask[b] = h->dXm[b];
   }
   p.G = h->dG;
+  p.Gtab = h->dGtab;
+  p.Gok = h->dGok;
   p.colsq = h->dColsq;
   p.Ppart = h->dPpart;
   p.Hpart = h->dHpart;
@@ -310,7 +316,8 @@ int variant_for(const nmf_handle* h) {
   if (!h->store_f32) return VAR_F64;
   if (h->forced_mode == 0) return VAR_F32;
   if (h->forced_mode == 1) return VAR_REF;
-  return h->phase ? VAR_REF : VAR_F32;
+  if (h->forced_mode == 2) return VAR_DF;
+  return h->phase ? VAR_DF : VAR_F32;
 }
 
 nmf_status read_state(nmf_handle* h) {
@@ -392,7 +399,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
     for (int j = 0; j < 3; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
   void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dY[0], h->dY[1],
-                   h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dColsq, h->dPpart,
+                   h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage};
   for (void* p : dptrs)
@@ -433,13 +440,15 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   h->has[VAR_F32] = get_kernels_f32(k, &h->ks[VAR_F32]);
   h->has[VAR_REF] = get_kernels_ref(k, &h->ks[VAR_REF]);
   h->has[VAR_F64] = get_kernels_f64(k, &h->ks[VAR_F64]);
+  h->has[VAR_DF] = get_kernels_df(k, &h->ks[VAR_DF]);
   for (int v = 0; v < NVAR; ++v)
     if (h->has[v])
       for (int ci = 0; ci < 4; ++ci)
         h->max_clusters[v][ci] = h->ks[v].max_clusters(1 << ci, (size_t)h->smem_optin);
   {
     // every variant this handle may run must have a plan for n
-    const int need[2] = {h->store_f32 ? VAR_F32 : VAR_F64, h->store_f32 ? VAR_REF : VAR_F64};
+    const int need[3] = {h->store_f32 ? VAR_F32 : VAR_F64, h->store_f32 ? VAR_REF : VAR_F64,
+                         h->store_f32 ? VAR_DF : VAR_F64};
     for (int v : need) {
       YPlan L;
       int msave = h->m;
@@ -468,6 +477,10 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
     ok &= dalloc(&h->dXm[b], h->n) == cudaSuccess;
   }
   ok &= dalloc(&h->dG, (size_t)k * k) == cudaSuccess;
+  if (k <= 8) {
+    ok &= dalloc(&h->dGtab, ((size_t)1 << k) * k * k) == cudaSuccess;
+    ok &= dalloc(&h->dGok, (size_t)1 << k) == cudaSuccess;
+  }
   ok &= dalloc(&h->dColsq, h->mcap) == cudaSuccess;
   ok &= cudaMalloc(&h->dPpart, (size_t)Qmax * h->ld * k * 8) == cudaSuccess;
   ok &= dalloc(&h->dHpart, (size_t)Qmax * k * k) == cudaSuccess;
@@ -663,7 +676,7 @@ nmf_status nmf_get_timing(nmf_handle* h, double* ypass_ms, int64_t* ypass_launch
 }
 
 nmf_status nmf_set_pass_mode(nmf_handle* h, int32_t mode) {
-  if (!h || mode < -1 || mode > 1) return NMF_EINVAL;
+  if (!h || mode < -1 || mode > 2) return NMF_EINVAL;
   h->forced_mode = mode;
   return NMF_OK;
 }

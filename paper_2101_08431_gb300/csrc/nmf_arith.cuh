@@ -1,0 +1,128 @@
+// Accumulation policies of the M pass (B = X^T M_tile and P += M_tile Y^T).
+//
+//   ArF32 : FP32 operands, FP32 FMA accumulation (bulk sweeps of the mixed form)
+//   ArF64 : FP64 operands and accumulation (the FP64 form, and the plain
+//           FP64-accumulated refinement of FP32 M)
+//   ArDF  : compensated FP32 ("double-float") accumulation of FP32 M times
+//           FP64 factors, for the refinement sweeps of the mixed form.  A
+//           factor value x is carried as hi + lo with hi = fl32(x),
+//           lo = fl32(x - hi); each term m * hi is formed exactly as p + e
+//           (p = fl(m hi), e = fma(m, hi, -p)), p is added to the running
+//           high word with Knuth's TwoSum (the rounding error is recovered
+//           exactly), and e, m * lo and the recovered errors go to the low
+//           word.  About 11 FP32 instructions per term instead of one FP64
+//           FMA, on a part whose FP32 rate is ~60x its FP64 rate; the sums
+//           carry ~44 significant bits.
+//
+// Every policy provides: V (staged factor value), A (accumulator), P (type
+// of the stored P partials), xval / yval (staging from FP64), zero, madd,
+// add, shfl_xor, to_double, to_p, and EPS (the epsilon of the NNLS entering
+// tolerance for sweeps computed with this policy).
+#pragma once
+
+#include "nmf_common.cuh"
+
+namespace nmfgb {
+
+struct DF {
+  float hi, lo;
+};
+
+struct ArF32 {
+  using V = float;
+  using A = float;
+  using P = float;
+  static constexpr bool XD = false;   // X is staged from its FP32 copy
+  static constexpr double EPS = 1.1920928955078125e-07;
+  __device__ static V xval(double, float x32) { return x32; }
+  __device__ static V yval(double y) { return (float)y; }
+  __device__ static A zero() { return 0.f; }
+  template <typename TM>
+  __device__ static A madd(TM m, V v, A a) { return __fmaf_rn((float)m, v, a); }
+  __device__ static A add(A a, A b) { return __fadd_rn(a, b); }
+  __device__ static A shfl_xor(A a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static double to_double(A a) { return (double)a; }
+  __device__ static P to_p(A a) { return a; }
+};
+
+struct ArF64 {
+  using V = double;
+  using A = double;
+  using P = double;
+  static constexpr bool XD = true;
+  static constexpr double EPS = 2.220446049250313e-16;
+  __device__ static V xval(double x, float) { return x; }
+  __device__ static V yval(double y) { return y; }
+  __device__ static A zero() { return 0.0; }
+  template <typename TM>
+  __device__ static A madd(TM m, V v, A a) { return __fma_rn((double)m, v, a); }
+  __device__ static A add(A a, A b) { return __dadd_rn(a, b); }
+  __device__ static A shfl_xor(A a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static double to_double(A a) { return a; }
+  __device__ static P to_p(A a) { return a; }
+};
+
+struct ArDF {
+  using V = DF;
+  using A = DF;
+  using P = double;
+  static constexpr bool XD = true;
+  static constexpr double EPS = 5.684341886080802e-14;   // 2^-44
+  __device__ static V split(double x) {
+    const float hi = __double2float_rn(x);
+    return {hi, __double2float_rn(x - (double)hi)};
+  }
+  __device__ static V xval(double x, float) { return split(x); }
+  __device__ static V yval(double y) { return split(y); }
+  __device__ static A zero() { return {0.f, 0.f}; }
+  // Knuth's TwoSum: s + err == a + b exactly.
+  __device__ static float two_sum(float a, float b, float& err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    err = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+    return s;
+  }
+  __device__ static A madd(float m, V v, A a) {
+    const float p = __fmul_rn(m, v.hi);
+    const float e = __fmaf_rn(m, v.hi, -p);            // m * v.hi == p + e exactly
+    float err;
+    const float s = two_sum(a.hi, p, err);
+    return {s, __fadd_rn(a.lo, __fadd_rn(err, __fmaf_rn(m, v.lo, e)))};
+  }
+  __device__ static A add(A a, A b) {
+    float err;
+    const float s = two_sum(a.hi, b.hi, err);
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+    const float h = __fadd_rn(s, lo);                   // renormalise (|s| >= |lo|)
+    return {h, __fadd_rn(lo, -__fadd_rn(h, -s))};
+  }
+  __device__ static A shfl_xor(A a, int o) {
+    return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+  }
+  __device__ static double to_double(A a) { return (double)a.hi + (double)a.lo; }
+  __device__ static P to_p(A a) { return to_double(a); }
+};
+
+// Reduce-scatter of VP = 2^p <= 32 accumulators held by every lane: lane l
+// ends with the warp-wide sum of accumulator (l & (VP-1)), in fixed order.
+template <typename AR, int VP>
+__device__ __forceinline__ typename AR::A warp_reduce_scatter_ar(typename AR::A (&v)[VP]) {
+  static_assert(VP >= 1 && VP <= 32 && (VP & (VP - 1)) == 0, "VP must be a power of two <= 32");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = VP / 2; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const typename AR::A keep = upper ? v[i + o] : v[i];
+      const typename AR::A send = upper ? v[i] : v[i + o];
+      v[i] = AR::add(keep, AR::shfl_xor(send, o));
+    }
+  }
+  typename AR::A r = v[0];
+#pragma unroll
+  for (int o = VP; o < 32; o <<= 1) r = AR::add(r, AR::shfl_xor(r, o));
+  return r;
+}
+
+}  // namespace nmfgb

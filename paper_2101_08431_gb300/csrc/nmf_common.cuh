@@ -63,6 +63,8 @@ struct Problem {
   uint32_t* ymask[2];     // passive set of each column
   uint32_t* xmask[2];     // passive set of each row
   double* G;              // k x k, X^T X of the current iterate
+  double* Gtab;           // k <= 8: inv(G_PP) for every passive set P (2^k x k x k)
+  int* Gok;               // k <= 8: 1 where the table entry is valid
   const double* colsq;    // ||M_{:,j}||^2 per physical column
   void* Ppart;            // [Q][ld][k] partial M Y^T (accumulate type)
   double* Hpart;          // [Q][k][k]
@@ -99,6 +101,41 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Arrive (release, cluster scope) on the mbarrier at the same offset in the
+// shared memory of cluster rank `rank`.
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, uint32_t rank) {
+  uint32_t raddr;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(smem_u32(bar)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(raddr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < SPIN_LIMIT; ++i)
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+  return false;
+}
+
+// Named barrier over the first `count` threads of the block (id != 0).
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -128,6 +165,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+
+// FP64 compares, min and max are several times slower than FP64 FMAs on
+// this part; for finite values the sign and order tests below run on the
+// IEEE bit patterns with integer instructions instead.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool dpos(double x) { return dbits(x) > 0; }            // x > 0
+__device__ __forceinline__ bool dneg(double x) { return dbits(x) < 0 && x != 0.0; } // x < 0
+// max of two non-negative values
+__device__ __forceinline__ double dmax_nn(double a, double b) { return dbits(a) >= dbits(b) ? a : b; }
+// w > t for t >= 0 (any w)
+__device__ __forceinline__ bool dgt_nn(double w, double t) { return dbits(w) > dbits(t); }
+// min(g, 0) and max(g, 0)
+__device__ __forceinline__ double dminz(double g) { return dbits(g) < 0 ? g : 0.0; }
+__device__ __forceinline__ double dmaxz(double g) { return dbits(g) > 0 ? g : 0.0; }
+__device__ __forceinline__ double dabs(double x) { return __longlong_as_double(dbits(x) & 0x7fffffffffffffffll); }
 
 // Fused multiply-add in the precision of the operands (no implicit promotion).
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }

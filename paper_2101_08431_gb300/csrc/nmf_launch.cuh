@@ -10,7 +10,8 @@ enum Variant {
   VAR_F32 = 0,   // FP32 M, FP32 contraction (mixed precision, bulk sweeps)
   VAR_REF = 1,   // FP32 M, FP64 contraction (mixed precision, refinement sweeps)
   VAR_F64 = 2,   // FP64 M, FP64 contraction (the plain FP64 form)
-  NVAR = 3
+  VAR_DF = 3,    // FP32 M, compensated FP32 contraction (mixed precision, refinement sweeps)
+  NVAR = 4
 };
 
 struct YPlan {
@@ -23,6 +24,7 @@ struct KernelSet {
   int (*max_clusters)(int C, size_t smem);   // co-resident clusters of the M pass
   cudaError_t (*xpass)(const Problem&, int mode, int Q, int nxblk, cudaStream_t);
   int TJ, RPT;
+  int rows;                                  // rows one CTA of the M pass can own
   size_t small_bytes;
   int tm_size;
 };
@@ -30,10 +32,11 @@ struct KernelSet {
 bool get_kernels_f32(int k, KernelSet* out);
 bool get_kernels_ref(int k, KernelSet* out);
 bool get_kernels_f64(int k, KernelSet* out);
+bool get_kernels_df(int k, KernelSet* out);
 
-template <typename TM, typename TA, int K>
+template <typename TM, typename AR, int K>
 cudaError_t launch_y(const Problem& p, int mode, const YPlan& L, cudaStream_t s) {
-  auto kern = ypass_kernel<TM, TA, K>;
+  auto kern = ypass_kernel<TM, AR, K>;
   static bool attr_done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -46,7 +49,7 @@ cudaError_t launch_y(const Problem& p, int mode, const YPlan& L, cudaStream_t s)
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.Q * L.C, 1, 1);
-  cfg.blockDim = dim3(YTraits<TM, TA, K>::T, 1, 1);
+  cfg.blockDim = dim3(YTraits<TM, AR, K>::T, 1, 1);
   cfg.dynamicSmemBytes = L.smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -61,16 +64,16 @@ cudaError_t launch_y(const Problem& p, int mode, const YPlan& L, cudaStream_t s)
 
 // How many clusters of C CTAs with `smem` bytes each the device can hold at
 // once (the M pass is persistent: a second wave would double its time).
-template <typename TM, typename TA, int K>
+template <typename TM, typename AR, int K>
 int max_clusters_y(int C, size_t smem) {
-  auto kern = ypass_kernel<TM, TA, K>;
+  auto kern = ypass_kernel<TM, AR, K>;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, 1, 1);
-  cfg.blockDim = dim3(YTraits<TM, TA, K>::T, 1, 1);
+  cfg.blockDim = dim3(YTraits<TM, AR, K>::T, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -89,27 +92,40 @@ int max_clusters_y(int C, size_t smem) {
 
 template <typename TA, int K>
 cudaError_t launch_x(const Problem& p, int mode, int Q, int nxblk, cudaStream_t s) {
-  xpass_kernel<TA, K><<<nxblk, XTraits<K>::T, 0, s>>>(p, mode, Q, nxblk, nullptr);
+  auto kern = xpass_kernel<TA, K>;
+  constexpr size_t dyn = XSmem<K>::bytes();
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dyn > 48 * 1024 && dev >= 0 && dev < 64 && !attr_done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    attr_done[dev] = true;
+  }
+  kern<<<nxblk, XTraits<K>::T, dyn, s>>>(p, mode, Q, nxblk, nullptr);
   return cudaGetLastError();
 }
 
-#define NMF_FILL(TM, TA, K)                                  \
+// TM: element type of M, AR: accumulation policy, PT: element type of the
+// P partials (read by the row pass)
+#define NMF_FILL(TM, AR, PT, K)                              \
   case K:                                                    \
-    out->ypass = launch_y<TM, TA, K>;                        \
-    out->max_clusters = max_clusters_y<TM, TA, K>;           \
-    out->xpass = launch_x<TA, K>;                            \
-    out->TJ = YTraits<TM, TA, K>::TJ;                        \
-    out->RPT = YTraits<TM, TA, K>::RPT;                      \
-    out->small_bytes = YSmem<TM, TA, K>::small_bytes();      \
+    out->ypass = launch_y<TM, AR, K>;                        \
+    out->max_clusters = max_clusters_y<TM, AR, K>;           \
+    out->xpass = launch_x<PT, K>;                            \
+    out->TJ = YTraits<TM, AR, K>::TJ;                        \
+    out->RPT = YTraits<TM, AR, K>::RPT;                      \
+    out->rows = YTraits<TM, AR, K>::ROWS;                    \
+    out->small_bytes = YSmem<TM, AR, K>::small_bytes();      \
     out->tm_size = (int)sizeof(TM);                          \
     return true;
 
-#define NMF_FILL_ALL(TM, TA)                                                              \
-  switch (k) {                                                                            \
-    NMF_FILL(TM, TA, 1) NMF_FILL(TM, TA, 2) NMF_FILL(TM, TA, 3) NMF_FILL(TM, TA, 4)       \
-    NMF_FILL(TM, TA, 5) NMF_FILL(TM, TA, 6) NMF_FILL(TM, TA, 7) NMF_FILL(TM, TA, 8)       \
-    NMF_FILL(TM, TA, 16)                                                                  \
-    default: return false;                                                                \
+#define NMF_FILL_ALL(TM, AR, PT)                                                                  \
+  switch (k) {                                                                                    \
+    NMF_FILL(TM, AR, PT, 1) NMF_FILL(TM, AR, PT, 2) NMF_FILL(TM, AR, PT, 3)                       \
+    NMF_FILL(TM, AR, PT, 4) NMF_FILL(TM, AR, PT, 5) NMF_FILL(TM, AR, PT, 6)                       \
+    NMF_FILL(TM, AR, PT, 7) NMF_FILL(TM, AR, PT, 8) NMF_FILL(TM, AR, PT, 16)                      \
+    default: return false;                                                                        \
   }
 
 }  // namespace nmfgb

@@ -28,8 +28,8 @@ namespace nmfgb {
 // two FMAs per step instead of the long FP64 divide.  Arguments outside the
 // FP32 normal range fall back to the division.
 __device__ __forceinline__ double rcp64(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  const long long ab = dbits(x) & 0x7fffffffffffffffll;   // |x| as an ordered integer
+  if (!(ab > 0x39b4484bfeebc2a0ll && ab < 0x4629c4ab5c06e0d3ll)) return 1.0 / x;   // 1e-30 .. 1e30
   double r = (double)__frcp_rn((float)x);
   double e = __fma_rn(-x, r, 1.0);
   r = __fma_rn(r, e, r);
@@ -68,7 +68,7 @@ struct NnlsSolver {
     G = Gs;
     double g = 0.0;
 #pragma unroll
-    for (int a = 0; a < K; ++a) g = fmax(g, Gs[a * K + a]);
+    for (int a = 0; a < K; ++a) g = dmax_nn(g, dabs(Gs[a * K + a]));
     gmax = g;
     pivot_min = 1e-14 * g;
     eps = eps_;
@@ -298,6 +298,160 @@ struct NnlsSolver {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Subset-inverse table (k <= 8): inv(G_PP) for every nonempty passive set P,
+// entry P at tab[P * K * K] (row-major K x K, meaningful on P x P only).
+// Built upward: the entry of P is the entry of P minus its highest index h,
+// bordered with h (one reciprocal, O(K^2) FMAs) -- the same pivots as a
+// Cholesky factorization of G_PP in ascending index order, so the oracle's
+// pivot test applies unchanged.  All subsets of one level are built in
+// parallel, so the dependency depth is K bordering steps.  ok[P] = 0 marks a
+// subset whose pivot failed (or that inherits a failure).
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ void build_subset_table(const NnlsSolver<K>& S, double* tab, int* ok) {
+  constexpr int NS = 1 << K;
+  for (int L = 1; L <= K; ++L) {
+    for (int P = (int)threadIdx.x; P < NS; P += (int)blockDim.x) {
+      if (P == 0 || __popc(P) != L) continue;
+      const int h = 31 - __clz(P);
+      const int parent = P & ~(1 << h);
+      double* A = tab + (size_t)P * K * K;
+      bool good = true;
+      if (parent) {
+        const double* B = tab + (size_t)parent * K * K;
+#pragma unroll
+        for (int e = 0; e < K * K; ++e) A[e] = B[e];
+        good = ok[parent] != 0;
+      }
+      good = good && S.add(A, (uint32_t)parent, h);
+      ok[P] = good ? 1 : 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Lawson-Hanson driven by the subset table: every solve on a passive set P
+// is z0 = A_P b_P followed by one step of iterative refinement
+// z = z0 + A_P (b - G z0)_P, so the result is accurate even though the
+// table entries were built by repeated bordering.  The entering test uses
+// the residual b - G z0.  Returns 0 converged, 1 iteration cap, -1 when a
+// needed table entry is marked degenerate (the caller then falls back to the
+// incremental solver).
+template <int K>
+__device__ __forceinline__ int table_nnls(const NnlsSolver<K>& S, const double* tab, const int* ok,
+                                          const double (&b)[K], double (&y)[K], bool warm,
+                                          uint32_t* mask_out) {
+  uint32_t P = 0, blocked = 0;
+  double bmax = 0.0;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    bmax = dmax_nn(bmax, dabs(b[a]));
+    if (warm && dpos(y[a])) P |= 1u << a;
+    else y[a] = 0.0;
+  }
+  int t_in = -1;
+  int status = 1;
+#pragma unroll 1
+  for (int it = 0; it < 6 * K + 12; ++it) {
+    double z[K], r[K];
+    if (P) {
+      if (!ok[P]) return -1;
+      const double* A = tab + (size_t)P * K * K;
+      double z0[K], rp[K];
+#pragma unroll
+      for (int a = 0; a < K; ++a) z0[a] = ((P >> a) & 1u) ? dot_masked<K>(A + a * K, b, P) : 0.0;
+#pragma unroll
+      for (int a = 0; a < K; ++a) r[a] = b[a] - dot_masked<K>(S.G + a * K, z0, P);
+#pragma unroll
+      for (int a = 0; a < K; ++a) rp[a] = ((P >> a) & 1u) ? r[a] : 0.0;
+#pragma unroll
+      for (int a = 0; a < K; ++a) z[a] = ((P >> a) & 1u) ? z0[a] + dot_masked<K>(A + a * K, rp, P) : 0.0;
+    } else {
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        z[a] = 0.0;
+        r[a] = b[a];
+      }
+    }
+    uint32_t nonpos = 0;   // passive variables whose value is not positive
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+      if (((P >> a) & 1u) && !dpos(z[a])) nonpos |= 1u << a;
+    if (t_in >= 0) {          // the entering variable must come out positive
+      const int tt = t_in;
+      t_in = -1;
+      if ((nonpos >> tt) & 1u) {
+        P &= ~(1u << tt);
+        blocked |= 1u << tt;
+        continue;             // y unchanged (y_tt = 0); re-solve on P
+      }
+    }
+    if (nonpos) {
+      // step from y towards z until the first passive variable reaches zero
+      double alpha = 2.0;
+      int q = -1;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        if (!((nonpos >> a) & 1u)) continue;
+        const double rr = y[a] * rcp64(y[a] - z[a]);
+        if (rr < alpha) {
+          alpha = rr;
+          q = a;
+        }
+      }
+      if (q < 0) {
+        alpha = 0.0;
+        q = __ffs(nonpos) - 1;
+      }
+      uint32_t drop = 1u << q;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        if (!((P >> a) & 1u)) continue;
+        y[a] = fmad(alpha, z[a] - y[a], y[a]);
+        if (!dpos(y[a])) drop |= 1u << a;
+      }
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+        if ((drop >> a) & 1u) y[a] = 0.0;
+      P &= ~drop;
+      continue;
+    }
+    double ymax = 0.0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      y[a] = ((P >> a) & 1u) ? z[a] : 0.0;
+      ymax = dmax_nn(ymax, y[a]);
+    }
+    // entering test on w = b - G y (the residual of the unrefined solve)
+    const double tol = 10.0 * K * S.eps * (bmax + S.gmax * ymax);
+    uint32_t cand = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+      if (!(((P | blocked) >> a) & 1u) && dgt_nn(r[a], tol)) cand |= 1u << a;
+    if (!cand) {
+      status = 0;
+      break;
+    }
+    int t = -1;
+    double best = tol;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+      if (((cand >> a) & 1u) && dgt_nn(r[a], best)) {
+        best = r[a];
+        t = a;
+      }
+    P |= 1u << t;
+    t_in = t;
+  }
+  uint32_t mask = 0;
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+    if (dpos(y[a])) mask |= 1u << a;
+  *mask_out = mask;
+  return status;
+}
+
 // Build the per-CTA inverse cache from up to CACHE_N sampled passive sets
 // (called by every thread of the block; G must be in shared memory).
 template <int K>
@@ -322,6 +476,31 @@ __device__ void build_cache(InvCache<K>* cache, const NnlsSolver<K>& S, const ui
     if (Q != cache->mask[e]) cache->mask[e] = 0xffffffffu;   // degenerate: never matches
   }
   __syncthreads();
+}
+
+// Warp-level version of build_cache (called by the 32 lanes of one warp).
+template <int K>
+__device__ void build_cache_warp(InvCache<K>* cache, const NnlsSolver<K>& S, const uint32_t* samples,
+                                 int nsamples) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    int n = 0;
+    for (int s = 0; s < nsamples; ++s) {
+      const uint32_t msk = samples[s];
+      if (!msk) continue;
+      bool seen = false;
+      for (int e = 0; e < n; ++e) seen |= cache->mask[e] == msk;
+      if (!seen && n < CACHE_N) cache->mask[n++] = msk;
+    }
+    cache->n = n;
+  }
+  __syncwarp();
+  if (lane < cache->n) {
+    uint32_t blocked = 0;
+    const uint32_t Q = S.build(cache->inv[lane], cache->mask[lane], &blocked);
+    if (Q != cache->mask[lane]) cache->mask[lane] = 0xffffffffu;
+  }
+  __syncwarp();
 }
 
 }  // namespace nmfgb

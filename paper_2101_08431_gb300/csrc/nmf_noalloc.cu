@@ -102,7 +102,7 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   int C = 1, R = 0;
   for (C = 1; C <= 8; C <<= 1) {
     R = ((ld + C - 1) / C + 31) / 32 * 32;
-    if (R <= ks.RPT * YTraits<float, double, 1>::T) break;
+    if (R <= ks.rows) break;
   }
   if (C > 8) return NMF_ECAPACITY;
   YPlan L;
@@ -114,7 +114,7 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   const size_t stage = (size_t)ks.TJ * R * sizeof(float);
   long long S = ((long long)optin - (long long)ks.small_bytes) / (long long)stage;
   S = std::min<long long>(std::min<long long>(S, 8), ntiles);
-  if (S < 1) return NMF_ECAPACITY;
+  if (S < (ntiles > 1 ? 2 : 1)) return NMF_ECAPACITY;
   L.S = (int)S;
   L.smem = ks.small_bytes + (size_t)S * stage;
 
@@ -123,6 +123,8 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   size_t off = 0;
   DevState* st = reinterpret_cast<DevState*>(b + take(off, sizeof(DevState)));
   double* G = reinterpret_cast<double*>(b + take(off, sizeof(double) * NA_KMAX * NA_KMAX));
+  double* Gtab = reinterpret_cast<double*>(b + take(off, sizeof(double) * (1 << NA_KMAX) * NA_KMAX * NA_KMAX));
+  int* Gok = reinterpret_cast<int*>(b + take(off, sizeof(int) * (1 << NA_KMAX)));
   double* colsq = reinterpret_cast<double*>(b + take(off, sizeof(double) * NA_MMAX));
   double* Xn = reinterpret_cast<double*>(b + take(off, sizeof(double) * NA_NMAX * NA_KMAX));
   float* X32a = reinterpret_cast<float*>(b + take(off, sizeof(float) * NA_NMAX * NA_KMAX));
@@ -159,6 +161,8 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   p.xmask[0] = xm0;
   p.xmask[1] = xm1;
   p.G = G;
+  p.Gtab = Gtab;
+  p.Gok = Gok;
   p.colsq = colsq;
   p.Ppart = Ppart;
   p.Hpart = Hpart;

@@ -19,20 +19,25 @@
 //            (Sec. 5.1), with no second read of M.
 #pragma once
 
+#include "nmf_arith.cuh"
 #include "nmf_nnls.cuh"
 
 namespace nmfgb {
 
-// Compile-time tile shape of the M pass.
-template <typename TM, typename TA, int K>
+// Compile-time tile shape of the M pass (AR: accumulation policy).  The CTA
+// has NCW compute warps (rows, contraction, P update) and one NNLS warp.
+template <typename TM, typename AR, int K>
 struct YTraits {
-  static constexpr bool FP64A = sizeof(TA) == 8;
+  static constexpr bool WIDE = sizeof(typename AR::V) == 8;   // 8-byte staged factors
   static constexpr int T = 512;
-  static constexpr int RPT = FP64A ? (K <= 8 ? 2 : 1) : (K <= 4 ? 6 : (K <= 8 ? 4 : 2));
-  static constexpr int TJ = FP64A ? (K <= 4 ? 4 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 8 : (K <= 8 ? 4 : 2));
+  static constexpr int NCW = 15;                               // compute warps
+  static constexpr int TC = NCW * 32;                          // compute threads
+  static constexpr int RPT = WIDE ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 7 : (K <= 8 ? 4 : 2));
+  static constexpr int TJ = WIDE ? (K <= 4 ? 4 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 8 : (K <= 8 ? 4 : 2));
   static constexpr int V = TJ * K;
   static constexpr int VP = (V <= 1) ? 1 : (V <= 2) ? 2 : (V <= 4) ? 4 : (V <= 8) ? 8 : (V <= 16) ? 16 : 32;
   static_assert(V <= 32, "B tile must fit one warp reduce-scatter");
+  static constexpr int ROWS = RPT * TC;                        // rows per CTA at most
 };
 
 __host__ __device__ inline int wrap_col(int head, int j, int mcap) {
@@ -41,35 +46,42 @@ __host__ __device__ inline int wrap_col(int head, int j, int mcap) {
 }
 
 // Shared-memory layout of the M pass (dynamic smem, 128-byte aligned parts).
-template <typename TM, typename TA, int K>
+template <typename TM, typename AR, int K>
 struct YSmem {
-  using Tr = YTraits<TM, TA, K>;
-  static constexpr int NW = Tr::T / 32;
+  using Tr = YTraits<TM, AR, K>;
   struct Small {
     uint64_t full[8];                  // stage barriers (S <= 8)
+    uint64_t bready[2];                // B of a tile reduced (compute -> NNLS warp)
+    uint64_t yready[2];                // y of a tile solved (NNLS warp -> compute)
+    uint64_t xbar[2];                  // cluster exchange of B partials
     double G[K * K];
     double Hacc[K * K];
-    double Bfull[Tr::VP];
+    double Bfull[2][Tr::VP];
     double Bpart[Tr::VP];
-    double red[NW][Tr::VP];
+    double red[Tr::NCW][Tr::VP];
     double xch[2][8][Tr::VP];          // cluster exchange slots (C <= 8)
-    double ybufD[Tr::TJ][K];
-    TA ybufA[Tr::TJ][K];
+    double ybufD[2][Tr::TJ][K];
+    typename AR::V ybufA[2][Tr::TJ][K];
+    double yt[Tr::TJ][NYT];            // per-column-lane KKT / objective terms
     uint32_t samples[CACHE_N];
-    double yt[Tr::TJ][NYT];            // per-column-thread KKT / objective terms
-    InvCache<K> cache;
+    InvCache<K> cache;                 // k > 8 only (no subset table)
+    double gtab[(K <= 6) ? (1 << K) * K * K : 1];   // subset table of G, staged (k <= 6)
+    int gok[(K <= 6) ? (1 << K) : 1];
   };
   static constexpr size_t SMALL_BYTES = (sizeof(Small) + 127) & ~size_t(127);
   __host__ __device__ static constexpr size_t small_bytes() { return SMALL_BYTES; }
   __host__ __device__ static size_t stage_bytes(int R) { return size_t(Tr::TJ) * R * sizeof(TM); }
 };
 
-template <typename TM, typename TA, int K>
+template <typename TM, typename AR, int K>
 __global__ void __launch_bounds__(512, 1)
     ypass_kernel(Problem p, int mode, int S, int C, int R, int Q) {
-  using Tr = YTraits<TM, TA, K>;
-  using Sm = YSmem<TM, TA, K>;
-  constexpr int T = Tr::T, RPT = Tr::RPT, TJ = Tr::TJ, VP = Tr::VP;
+  using Tr = YTraits<TM, AR, K>;
+  using Sm = YSmem<TM, AR, K>;
+  using VT = typename AR::V;
+  using AT = typename AR::A;
+  constexpr int TC = Tr::TC, NCW = Tr::NCW, RPT = Tr::RPT, TJ = Tr::TJ, VP = Tr::VP;
+  constexpr bool TABLE = K <= 8;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   typename Sm::Small& sm = *reinterpret_cast<typename Sm::Small*>(smem_raw);
   TM* stages = reinterpret_cast<TM*>(smem_raw + Sm::small_bytes());
@@ -92,9 +104,15 @@ __global__ void __launch_bounds__(512, 1)
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&sm.full[s], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.bready[b], 1);
+      mbar_init(&sm.yready[b], 1);
+      mbar_init(&sm.xbar[b], (uint32_t)(C * VP));
+    }
     fence_mbar_init();
   }
-  __syncthreads();
+  if (C > 1) cluster.sync();
+  else __syncthreads();
 
   auto issue = [&](int t, int s) {
     const int tj = min(TJ, ncols - t * TJ);
@@ -108,169 +126,237 @@ __global__ void __launch_bounds__(512, 1)
       }
     }
   };
-  if (tid == 0)
-    for (int t = 0; t < min(S, ntiles); ++t) issue(t, t);
-
-  // G, the rows of X owned by this thread, accumulators
-  if (tid < K * K) {
-    sm.G[tid] = p.G[tid];
-    sm.Hacc[tid] = 0.0;
-  }
-  TA xr[RPT][K];
-  TA pacc[RPT][K];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int row = r0 + tid + r * T;
-    const bool ok = (tid + r * T) < rows_c && row < p.n;
-#pragma unroll
-    for (int a = 0; a < K; ++a) {
-      TA v = TA(0);
-      if (ok) {
-        if (Tr::FP64A) v = (TA)p.X[cur][(size_t)row * K + a];
-        else v = (TA)p.X32[cur][(size_t)row * K + a];
-      }
-      xr[r][a] = v;
-      pacc[r][a] = TA(0);
-    }
-  }
-  // passive sets of sampled columns of this cluster -> inverse cache
-  if (tid < CACHE_N) {
-    uint32_t msk = 0;
-    if (mode == MODE_SWEEP && p.warm && ncols > 0) {
-      const int j = c0 + (int)(((long long)tid * ncols) / CACHE_N);
-      msk = p.ymask[cur][wrap_col(p.head, j, p.mcap)];
-    }
-    sm.samples[tid] = msk;
-  }
-  __syncthreads();
-  NnlsSolver<K> solver;
-  solver.init(sm.G, Tr::FP64A ? 2.220446049250313e-16 : 1.1920928955078125e-07);
-  if (mode == MODE_SWEEP) build_cache<K>(&sm.cache, solver, sm.samples, CACHE_N);
-  else if (tid == 0) sm.cache.n = 0;
-
-  if (tid < TJ)
-    for (int e = 0; e < NYT; ++e) sm.yt[tid][e] = 0.0;
-  double Ascr[K * K];
   bool timed_out = false;
 
-  for (int t = 0; t < ntiles; ++t) {
-    const int s = t % S;
-    const uint32_t parity = (uint32_t)((t / S) & 1);
-    const int tj = min(TJ, ncols - t * TJ);
-    // the column threads fetch their warm start before the contraction, so
-    // the load latency hides behind it
-    double yo[K];
-    uint32_t old_mask = 0;
-    int phys = 0;
-    if (tid < tj) {
-      phys = wrap_col(p.head, c0 + t * TJ + tid, p.mcap);
-#pragma unroll
-      for (int a = 0; a < K; ++a) yo[a] = p.Y[cur][(size_t)phys * K + a];
-      old_mask = p.ymask[cur][phys];
-    }
-    if (!mbar_wait(&sm.full[s], parity)) timed_out = true;
-    const TM* tile = stages + (size_t)s * TJ * R;
-
-    // ---- B partial = X_rows^T M_tile over this thread's rows
-    TA acc[VP];
-#pragma unroll
-    for (int e = 0; e < VP; ++e) acc[e] = TA(0);
+  if (warp < NCW) {
+    // ======================= compute warps ==================================
+    if (tid == 0)
+      for (int t = 0; t < min(S, ntiles); ++t) issue(t, t);
+    if (tid < K * K) sm.Hacc[tid] = 0.0;
+    VT xr[RPT][K];
+    AT pacc[RPT][K];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int rr = tid + r * T;
-      if (rr < rows_c) {
+      const int row = r0 + tid + r * TC;
+      const bool ok = (tid + r * TC) < rows_c && row < p.n;
 #pragma unroll
-        for (int jj = 0; jj < TJ; ++jj) {
-          const TA mv = (TA)tile[(size_t)jj * R + rr];
-#pragma unroll
-          for (int a = 0; a < K; ++a) acc[jj * K + a] = fmad(mv, xr[r][a], acc[jj * K + a]);
+      for (int a = 0; a < K; ++a) {
+        double xd = 0.0;
+        float xf = 0.f;
+        if (ok) {
+          if (AR::XD) xd = p.X[cur][(size_t)row * K + a];
+          else xf = p.X32[cur][(size_t)row * K + a];
         }
+        xr[r][a] = AR::xval(xd, xf);
+        pacc[r][a] = AR::zero();
       }
     }
-    {
-      const TA wsum = warp_reduce_scatter<VP, TA>(acc);
-      if (lane < VP) sm.red[warp][lane] = (double)wsum;
-    }
-    __syncthreads();
-    const int slot = t & 1;
-    if (tid < ((4 * VP + 31) & ~31)) {   // whole warps take part in the shuffles
-      // value tid/4: lane quad g adds warps g, g+4, ... then a quad tree
-      // (short FP64 chains, fixed order)
-      const int v = tid >> 2, g = tid & 3;
-      double bs = 0.0;
-      if (v < VP) {
+    // Iteration t contracts tile t (t < ntiles) and then accumulates tile
+    // t - 1 (t >= 1) once the NNLS warp has solved it: P += M_tile Y_tile^T
+    // on the own rows and H += Y_tile Y_tile^T.  One code path keeps the row
+    // accumulators in registers.
+    for (int t = 0; t <= ntiles; ++t) {
+      if (t < ntiles) {
+        const int s = t % S, slot = t & 1;
+        if (!mbar_wait(&sm.full[s], (uint32_t)((t / S) & 1))) timed_out = true;
+        const TM* tile = stages + (size_t)s * TJ * R;
+        // ---- B partial = X_rows^T M_tile over this thread's rows
+        AT acc[VP];
 #pragma unroll
-        for (int w = g; w < Sm::NW; w += 4) bs += sm.red[w][v];
-      }
-      bs += __shfl_xor_sync(0xffffffffu, bs, 1);
-      bs += __shfl_xor_sync(0xffffffffu, bs, 2);
-      if (g == 0 && v < VP) sm.Bpart[v] = bs;
-    }
-    __syncthreads();
-    if (tid < VP) {
-      const double bs = sm.Bpart[tid];
-      if (C > 1) {
-        for (int rk = 0; rk < C; ++rk) {
-          double* dst = cluster.map_shared_rank(&sm.xch[slot][crank][tid], rk);
-          *dst = bs;
+        for (int e = 0; e < VP; ++e) acc[e] = AR::zero();
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int rr = tid + r * TC;
+          if (rr < rows_c) {
+#pragma unroll
+            for (int jj = 0; jj < TJ; ++jj) {
+              const TM mv = tile[(size_t)jj * R + rr];
+#pragma unroll
+              for (int a = 0; a < K; ++a) acc[jj * K + a] = AR::madd(mv, xr[r][a], acc[jj * K + a]);
+            }
+          }
         }
-      } else {
-        sm.Bfull[tid] = bs;
+        {
+          const AT wsum = warp_reduce_scatter_ar<AR, VP>(acc);
+          if (lane < VP) sm.red[warp][lane] = AR::to_double(wsum);
+        }
+        named_sync(1, TC);
+        if (tid < ((4 * VP + 31) & ~31)) {      // 4 lanes per value, then a quad tree
+          const int v = tid >> 2, g = tid & 3;
+          double bs = 0.0;
+          if (v < VP) {
+#pragma unroll
+            for (int w = g; w < NCW; w += 4) bs += sm.red[w][v];
+          }
+          bs += __shfl_xor_sync(0xffffffffu, bs, 1);
+          bs += __shfl_xor_sync(0xffffffffu, bs, 2);
+          if (g == 0 && v < VP) {
+            if (C > 1) {
+              // push this CTA's partial to every CTA of the cluster
+              for (int rk = 0; rk < C; ++rk) {
+                double* dst = cluster.map_shared_rank(&sm.xch[slot][crank][v], rk);
+                *dst = bs;
+                mbar_arrive_remote(&sm.xbar[slot], (uint32_t)rk);
+              }
+            } else {
+              sm.Bfull[slot][v] = bs;
+            }
+          }
+        }
+        if (C > 1) {
+          if (!mbar_wait_cluster(&sm.xbar[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
+          if (tid < VP) {
+            double bs = 0.0;
+            for (int c = 0; c < C; ++c) bs += sm.xch[slot][c][tid];
+            sm.Bfull[slot][tid] = bs;
+          }
+        }
+        named_sync(1, TC);
+        if (tid == 0) mbar_arrive(&sm.bready[slot]);
+      }
+      if (t >= 1) {
+        const int u = t - 1, ub = u & 1;
+        if (!mbar_wait(&sm.yready[ub], (uint32_t)((u >> 1) & 1))) timed_out = true;
+        if (mode != MODE_KKT) {
+          const int tj = min(TJ, ncols - u * TJ);
+          const TM* tile = stages + (size_t)(u % S) * TJ * R;
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) {
+            const int rr = tid + r * TC;
+            if (rr < rows_c) {
+#pragma unroll
+              for (int jj = 0; jj < TJ; ++jj) {
+                if (jj < tj) {
+                  const TM mv = tile[(size_t)jj * R + rr];
+#pragma unroll
+                  for (int a = 0; a < K; ++a) pacc[r][a] = AR::madd(mv, sm.ybufA[ub][jj][a], pacc[r][a]);
+                }
+              }
+            }
+          }
+          if (tid >= 32 && tid < 32 + K * K) {     // pairwise tree over the tile's columns
+            const int e = tid - 32, a = e / K, c = e % K;
+            double hp[TJ];
+#pragma unroll
+            for (int jj = 0; jj < TJ; ++jj) hp[jj] = jj < tj ? sm.ybufD[ub][jj][a] * sm.ybufD[ub][jj][c] : 0.0;
+#pragma unroll
+            for (int w = 1; w < TJ; w <<= 1)
+#pragma unroll
+              for (int jj = 0; jj + w < TJ; jj += 2 * w) hp[jj] += hp[jj + w];
+            sm.Hacc[e] += hp[0];
+          }
+        }
+        named_sync(1, TC);                       // every compute thread is done with stage u % S
+        if (tid == 0 && u + S < ntiles) issue(u + S, u % S);
       }
     }
-    if (C > 1) {
-      cluster.sync();
-      if (tid < VP) {
-        double bs = 0.0;
-        for (int c = 0; c < C; ++c) bs += sm.xch[slot][c][tid];
-        sm.Bfull[tid] = bs;
-      }
-    }
-    __syncthreads();
 
-    // ---- one NNLS per column (threads 0..tj-1 of warp 0)
-    if (tid < TJ) {
-      double yn[K];
+    // ---- epilogue: partials of this cluster
+    typename AR::P* Pp = static_cast<typename AR::P*>(p.Ppart);
+    if (mode != MODE_KKT) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int rr = tid + r * TC;
+        const int row = r0 + rr;
+        if (rr < rows_c && row < p.n) {
+#pragma unroll
+          for (int a = 0; a < K; ++a) Pp[((size_t)q * p.ld + row) * K + a] = AR::to_p(pacc[r][a]);
+        }
+      }
+    }
+    if (crank == 0) {
+      if (tid < K * K) p.Hpart[(size_t)q * K * K + tid] = (mode == MODE_KKT) ? 0.0 : sm.Hacc[tid];
+      if (tid < NYT) {   // fixed-order combine of the column lanes' terms
+        double v = sm.yt[0][tid];
+        for (int jj = 1; jj < TJ; ++jj) v = (tid == YT_YMAX) ? fmax(v, sm.yt[jj][tid]) : v + sm.yt[jj][tid];
+        p.Yterms[(size_t)q * NYT + tid] = v;
+      }
+    }
+  } else {
+    // ======================= NNLS warp ======================================
+    for (int e = lane; e < K * K; e += 32) sm.G[e] = p.G[e];
+    if (K <= 6 && mode == MODE_SWEEP) {
+      for (int e = lane; e < (1 << K) * K * K; e += 32) sm.gtab[e] = p.Gtab[e];
+      for (int e = lane; e < (1 << K); e += 32) sm.gok[e] = p.Gok[e];
+    }
+    if (lane < TJ)
+      for (int e = 0; e < NYT; ++e) sm.yt[lane][e] = 0.0;
+    if (!TABLE) {
+      if (lane < CACHE_N) {
+        uint32_t msk = 0;
+        if (mode == MODE_SWEEP && p.warm && ncols > 0) {
+          const int j = c0 + (int)(((long long)lane * ncols) / CACHE_N);
+          msk = p.ymask[cur][wrap_col(p.head, j, p.mcap)];
+        }
+        sm.samples[lane] = msk;
+      }
+      if (lane == 0) sm.cache.n = 0;
+    }
+    __syncwarp();
+    NnlsSolver<K> solver;
+    solver.init(sm.G, AR::EPS);
+    if (!TABLE && mode == MODE_SWEEP) build_cache_warp<K>(&sm.cache, solver, sm.samples, CACHE_N);
+    double Ascr[K * K];
+    for (int t = 0; t < ntiles; ++t) {
+      const int slot = t & 1;
+      const int tj = min(TJ, ncols - t * TJ);
+      double yo[K], yn[K];
+      uint32_t old_mask = 0;
+      int phys = 0;
+      if (lane < tj) {   // warm start and passive set, fetched before B is ready
+        phys = wrap_col(p.head, c0 + t * TJ + lane, p.mcap);
+#pragma unroll
+        for (int a = 0; a < K; ++a) yo[a] = p.Y[cur][(size_t)phys * K + a];
+        old_mask = p.ymask[cur][phys];
+      }
+      if (!mbar_wait(&sm.bready[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
 #pragma unroll
       for (int a = 0; a < K; ++a) yn[a] = 0.0;
-      if (tid < tj) {
+      if (lane < tj) {
         double b[K];
 #pragma unroll
-        for (int a = 0; a < K; ++a) b[a] = sm.Bfull[tid * K + a];
+        for (int a = 0; a < K; ++a) b[a] = sm.Bfull[slot][lane * K + a];
+        double* yt = sm.yt[lane];
         if (mode != MODE_PRIME) {
           // Y-half KKT terms of the incoming iterate: g = G y - b
-          double bn = 0.0, by = 0.0, ygy = 0.0, ymax = 0.0, yn2 = 0.0, neg = 0.0, comp = 0.0;
+          double neg = 0.0, comp = 0.0, bn = 0.0, by = 0.0, ygy = 0.0, ymax = 0.0, yn2 = 0.0;
 #pragma unroll
           for (int a = 0; a < K; ++a) {
             const double g = dot_masked<K>(sm.G + a * K, yo, 0xffffffffu) - b[a];
-            const double mn = fmin(g, 0.0), pos = fmax(g, 0.0) * yo[a];
+            const double mn = dminz(g), pos = dmaxz(g) * yo[a];
             neg = fmad(mn, mn, neg);
             comp = fmad(pos, pos, comp);
             bn = fmad(b[a], b[a], bn);
             by = fmad(b[a], yo[a], by);
             ygy = fmad(yo[a], g + b[a], ygy);
-            ymax = fmax(ymax, yo[a]);
+            ymax = dmax_nn(ymax, yo[a]);
             yn2 = fmad(yo[a], yo[a], yn2);
             if (!isfinite(b[a])) set_err(st, ERR_NONFINITE);
           }
-          double* yt = sm.yt[tid];
           yt[YT_NEG] += neg;
           yt[YT_COMP] += comp;
           yt[YT_BNORM2] += bn;
           yt[YT_BY] += by;
           yt[YT_YGY] += ygy;
-          yt[YT_YMAX] = fmax(yt[YT_YMAX], ymax);
+          yt[YT_YMAX] = dmax_nn(yt[YT_YMAX], ymax);
           yt[YT_YNORM2] += yn2;
         }
         if (mode == MODE_SWEEP) {
 #pragma unroll
           for (int a = 0; a < K; ++a) yn[a] = yo[a];
           uint32_t msk = 0;
-          const int stt = solver.solve(Ascr, b, yn, p.warm != 0, &sm.cache, &msk);
+          int stt = -1;
+          if (TABLE)
+            stt = table_nnls<K>(solver, K <= 6 ? sm.gtab : p.Gtab, K <= 6 ? sm.gok : p.Gok, b, yn,
+                                p.warm != 0, &msk);
+          if (stt < 0) {
+#pragma unroll
+            for (int a = 0; a < K; ++a) yn[a] = yo[a];
+            stt = solver.solve(Ascr, b, yn, p.warm != 0, TABLE ? nullptr : &sm.cache, &msk);
+          }
           double d2 = 0.0;
 #pragma unroll
           for (int a = 0; a < K; ++a) d2 = fmad(yn[a] - yo[a], yn[a] - yo[a], d2);
-          double* yt = sm.yt[tid];
           yt[YT_DY2] += d2;
           yt[YT_CHANGED] += (old_mask != msk) ? 1.0 : 0.0;
           yt[YT_NOTCONV] += (double)stt;
@@ -289,68 +375,18 @@ __global__ void __launch_bounds__(512, 1)
           if (mode == MODE_PRIME && crank == 0) p.ymask[cur][phys] = msk;
         }
       }
+      if (lane < TJ) {
 #pragma unroll
-      for (int a = 0; a < K; ++a) {
-        sm.ybufD[tid][a] = yn[a];
-        sm.ybufA[tid][a] = (TA)yn[a];
-      }
-    }
-    __syncthreads();
-
-    // ---- P += M_tile Y_tile^T (own rows), H += Y_tile Y_tile^T
-    if (mode != MODE_KKT) {
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int rr = tid + r * T;
-        if (rr < rows_c) {
-#pragma unroll
-          for (int jj = 0; jj < TJ; ++jj) {
-            if (jj < tj) {
-              const TA mv = (TA)tile[(size_t)jj * R + rr];
-#pragma unroll
-              for (int a = 0; a < K; ++a) pacc[r][a] = fmad(mv, sm.ybufA[jj][a], pacc[r][a]);
-            }
-          }
+        for (int a = 0; a < K; ++a) {
+          sm.ybufD[slot][lane][a] = yn[a];
+          sm.ybufA[slot][lane][a] = AR::yval(yn[a]);
         }
       }
-      if (tid >= 32 && tid < 32 + K * K) {     // H += sum_jj y_jj y_jj^T as a pairwise tree
-        const int e = tid - 32, a = e / K, c = e % K;
-        double hp[TJ];
-#pragma unroll
-        for (int jj = 0; jj < TJ; ++jj) hp[jj] = jj < tj ? sm.ybufD[jj][a] * sm.ybufD[jj][c] : 0.0;
-#pragma unroll
-        for (int w = 1; w < TJ; w <<= 1)
-#pragma unroll
-          for (int jj = 0; jj + w < TJ; jj += 2 * w) hp[jj] += hp[jj + w];
-        sm.Hacc[e] += hp[0];
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.yready[slot]);
     }
-    __syncthreads();
-    if (tid == 0 && t + S < ntiles) issue(t + S, s);
   }
   if (timed_out) set_err(st, ERR_TIMEOUT);
-
-  // ---- epilogue: partials of this cluster
-  TA* Pp = static_cast<TA*>(p.Ppart);
-  if (mode != MODE_KKT) {
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int rr = tid + r * T;
-      const int row = r0 + rr;
-      if (rr < rows_c && row < p.n) {
-#pragma unroll
-        for (int a = 0; a < K; ++a) Pp[((size_t)q * p.ld + row) * K + a] = pacc[r][a];
-      }
-    }
-  }
-  if (crank == 0) {
-    if (tid < K * K) p.Hpart[(size_t)q * K * K + tid] = (mode == MODE_KKT) ? 0.0 : sm.Hacc[tid];
-    if (tid < NYT) {   // fixed-order combine of the column threads' terms
-      double v = sm.yt[0][tid];
-      for (int jj = 1; jj < TJ; ++jj) v = (tid == YT_YMAX) ? fmax(v, sm.yt[jj][tid]) : v + sm.yt[jj][tid];
-      p.Yterms[(size_t)q * NYT + tid] = v;
-    }
-  }
   if (C > 1) cluster.sync();
 }
 
@@ -418,27 +454,44 @@ __device__ void tree_sum(const double* src, int nparts, size_t stride, int nval,
         w[u] = (ok && q < nparts) ? src[(size_t)q * stride + e] : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) r = is_max ? fmax(r, w[u]) : r + w[u];
+      for (int u = 0; u < U; ++u) r = is_max ? dmax_nn(r, w[u]) : r + w[u];
     }
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) {
       const double w = __shfl_xor_sync(0xffffffffu, r, o);
-      r = is_max ? fmax(r, w) : r + w;
+      r = is_max ? dmax_nn(r, w) : r + w;
     }
     if (ok && g == 0) out[e] = r;
   }
 }
 
+// Dynamic shared memory of the row pass: the subset table of H (k <= 8).
+template <int K>
+struct XSmem {
+  static constexpr bool TABLE = K <= 8;
+  static constexpr size_t TAB = TABLE ? (size_t(1) << K) * K * K * sizeof(double) : 0;
+  static constexpr size_t OK = TABLE ? (size_t(1) << K) * sizeof(int) : 0;
+  static constexpr size_t bytes() { return TAB + OK + 16; }
+};
+
 // Row pass: rows [32 b, 32 b + 32) of X.  The 8 warps split the cluster
-// partials of P = M Y^T (lane <-> row, accumulated in the pass's precision),
-// warp 0 solves the 32 row NNLS problems and forms the X-half terms and the
-// Gram partial; the last block to finish combines the blocks.
+// partials of P = M Y^T (lane <-> row, accumulated in the pass's precision)
+// and build the subset table of H; warp 0 solves the 32 row NNLS problems
+// and forms the X-half terms and the Gram partial; the last block to finish
+// combines the blocks, forms G = X^T X and its subset table for the next
+// M pass, and the statistics of the iterate.
 template <typename TA, int K>
 __global__ void __launch_bounds__(XTraits<K>::T)
     xpass_kernel(Problem p, int mode, int Q, int nxblk, double* kkt_out) {
   using Tr = XTraits<K>;
+  using Xs = XSmem<K>;
   constexpr int T = Tr::T, NW = Tr::NW, RB = Tr::RB, NV = Tr::NV;
+  constexpr bool TABLE = Xs::TABLE;
+  extern __shared__ __align__(16) unsigned char xsm_raw[];
+  double* tab = reinterpret_cast<double*>(xsm_raw);
+  int* tok = reinterpret_cast<int*>(xsm_raw + Xs::TAB);
   __shared__ double H[K * K];
+  __shared__ double Gs[K * K];
   __shared__ TA psum[NW][RB][K];
   __shared__ double fin[NV];
   __shared__ double yfin[NYT];
@@ -455,7 +508,7 @@ __global__ void __launch_bounds__(XTraits<K>::T)
   const bool active = row < p.n;
 
   tree_sum<T>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
-  if (tid < CACHE_N) {
+  if (!TABLE && tid < CACHE_N) {
     uint32_t msk = 0;
     if (mode == MODE_SWEEP && p.warm) {
       const int nb = min(RB, p.n - row0);
@@ -488,7 +541,10 @@ __global__ void __launch_bounds__(XTraits<K>::T)
   __syncthreads();
   NnlsSolver<K> solver;
   solver.init(H, 2.220446049250313e-16);
-  if (mode == MODE_SWEEP) build_cache<K>(&cache, solver, samples, CACHE_N);
+  if (mode == MODE_SWEEP) {
+    if (TABLE) build_subset_table<K>(solver, tab, tok);
+    else build_cache<K>(&cache, solver, samples, CACHE_N);
+  }
 
   if (warp == 0) {
     double v[Tr::NVC * 32];
@@ -508,8 +564,14 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       uint32_t msk = 0;
       int stt = 0;
       if (mode == MODE_SWEEP) {
-        double Ascr[K * K];
-        stt = solver.solve(Ascr, pr, xn, p.warm != 0, &cache, &msk);
+        stt = -1;
+        if (TABLE) stt = table_nnls<K>(solver, tab, tok, pr, xn, p.warm != 0, &msk);
+        if (stt < 0) {
+          double Ascr[K * K];
+#pragma unroll
+          for (int a = 0; a < K; ++a) xn[a] = xo[a];
+          stt = solver.solve(Ascr, pr, xn, p.warm != 0, TABLE ? nullptr : &cache, &msk);
+        }
       } else {
 #pragma unroll
         for (int a = 0; a < K; ++a)
@@ -519,14 +581,12 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       double neg = 0.0, comp = 0.0, pn = 0.0, xmax = 0.0, xn2 = 0.0, dx2 = 0.0, xp = 0.0;
 #pragma unroll
       for (int a = 0; a < K; ++a) {
-        double g = -pr[a];
-#pragma unroll
-        for (int c = 0; c < K; ++c) g = fmad(H[a * K + c], xn[c], g);
-        const double mn = fmin(g, 0.0), pos = fmax(g, 0.0) * xn[a];
+        const double g = dot_masked<K>(H + a * K, xn, 0xffffffffu) - pr[a];
+        const double mn = dminz(g), pos = dmaxz(g) * xn[a];
         neg = fmad(mn, mn, neg);
         comp = fmad(pos, pos, comp);
         pn = fmad(pr[a], pr[a], pn);
-        xmax = fmax(xmax, xn[a]);
+        xmax = dmax_nn(xmax, xn[a]);
         xn2 = fmad(xn[a], xn[a], xn2);
         dx2 = fmad(xn[a] - xo[a], xn[a] - xo[a], dx2);
         xp = fmad(xn[a], pr[a], xp);
@@ -572,9 +632,9 @@ __global__ void __launch_bounds__(XTraits<K>::T)
         if (e < NV) p.Xpart[(size_t)blockIdx.x * NV + e] = (e == K * K + XT_XMAX) ? mx : r;
       }
     }
+    __threadfence();
   }
   // last block to finish: G for the next sweep, terms and statistics
-  __threadfence();
   __syncthreads();
   if (tid == 0) ticket = atomicAdd(&st->xblocks_done, 1u);
   __syncthreads();
@@ -583,7 +643,16 @@ __global__ void __launch_bounds__(XTraits<K>::T)
   tree_sum<T>(p.Xpart, nxblk, NV, NV, fin, K * K + XT_XMAX);
   tree_sum<T>(p.Yterms, Q, NYT, NYT, yfin, YT_YMAX);
   __syncthreads();
-  if (tid < K * K) p.G[tid] = fin[tid];
+  if (tid < K * K) {
+    p.G[tid] = fin[tid];
+    Gs[tid] = fin[tid];
+  }
+  __syncthreads();
+  if (TABLE) {   // subset table of the new G for the next M pass (global memory)
+    NnlsSolver<K> gs;
+    gs.init(Gs, 2.220446049250313e-16);
+    build_subset_table<K>(gs, p.Gtab, p.Gok);
+  }
   if (tid == 0) {
     double xt[NXT];
     for (int e = 0; e < NXT; ++e) xt[e] = fin[K * K + e];
