@@ -231,8 +231,8 @@ struct NnlsSolver {
   // and the solution on exit; A is per-thread scratch of K*K doubles.
   // Returns 0 when converged, 1 at the iteration cap.  *mask_out gets the
   // support of y.
-  __device__ int solve(double* A, const double (&b)[K], double (&y)[K], bool warm,
-                       const InvCache<K>* cache, uint32_t* mask_out) const {
+  __device__ __noinline__ int solve(double* A, const double (&b)[K], double (&y)[K], bool warm,
+                                    const InvCache<K>* cache, uint32_t* mask_out) const {
     uint32_t P = 0, blocked = 0;
     double bmax = 0.0;
 #pragma unroll
@@ -449,6 +449,160 @@ __device__ __forceinline__ int table_nnls(const NnlsSolver<K>& S, const double* 
   for (int a = 0; a < K; ++a)
     if (dpos(y[a])) mask |= 1u << a;
   *mask_out = mask;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// Lane-parallel Lawson-Hanson for k <= 8 with the subset table.
+//
+// FP64 on this part costs roughly one sub-partition FP64-unit pass per warp
+// instruction whatever the number of active lanes, so a solver that keeps
+// one column per lane pays for K-fold unrolled scalar work.  Here a warp
+// solves 32 / KP columns at once, lane = column slot * KP + component a
+// (KP = K rounded up to a power of two): every mat-vec is K FMAs per lane
+// with the other components fetched by shuffles (integer pipe), and every
+// per-column decision (feasibility, entering test, step ratio) is a ballot or
+// an integer max/min over the KP-lane group.
+// ---------------------------------------------------------------------------
+template <int K>
+struct LaneGroup {
+  static constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : 8;   // lanes per column
+  static constexpr int CPW = 32 / KP;                                    // columns per warp
+  static constexpr uint32_t GMASK = (KP == 32) ? 0xffffffffu : ((1u << KP) - 1u);
+  int lane, a, base;
+  __device__ void init() {
+    lane = threadIdx.x & 31;
+    a = lane & (KP - 1);
+    base = lane & ~(KP - 1);
+  }
+  __device__ double from(double v, int c) const { return __shfl_sync(0xffffffffu, v, base + c); }
+  // the group's bits of a warp ballot, bit a of the result = lane base + a
+  __device__ uint32_t bits(bool pred) const { return (__ballot_sync(0xffffffffu, pred) >> base) & GMASK; }
+  // max over the group of non-negative values (integer order of the bits)
+  __device__ double max_nn(double v) const {
+#pragma unroll
+    for (int o = 1; o < KP; o <<= 1) v = dmax_nn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  }
+};
+
+// Solve the columns held by the warp.  Per lane: b = component a of the
+// right-hand side, y = component a of the warm start (in) / solution (out),
+// grow = row a of G (K values, registers).  tab / ok: subset table of G.
+// Every collective (shuffle, ballot) is executed by all lanes in the same
+// order; the per-column state machine acts through predicates only.
+// Returns per lane the column's status (0 converged, 1 iteration cap, -1 a
+// needed table entry is degenerate) and its passive set in *mask.
+template <int K>
+__device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const double* tab, const int* ok,
+                                               const double (&grow)[K], double gmax, double eps,
+                                               double b, double& y, bool warm, bool active,
+                                               bool refine, uint32_t* mask) {
+  constexpr int KP = LaneGroup<K>::KP;
+  const bool comp = active && g.a < K;
+  double bc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) bc[c] = g.from(b, c);
+  const double bmax = g.max_nn(comp ? dabs(b) : 0.0);
+  const bool ypos = comp && warm && dpos(y);
+  uint32_t P = g.bits(ypos);
+  if (!ypos) y = 0.0;
+  uint32_t blocked = 0;
+  int t_in = -1, status = active ? 1 : 0;
+  bool done = !active;
+#pragma unroll 1
+  for (int it = 0; it < 6 * K + 12; ++it) {
+    if (P && !done && !ok[P]) {
+      status = -1;
+      done = true;
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+    const bool inP = !done && ((P >> g.a) & 1u);
+    const double* A = tab + (size_t)(inP ? P : 0) * K * K + g.a * K;
+    double z0 = 0.0;
+    if (inP) {
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        if ((P >> c) & 1u) z0 = fmad(A[c], bc[c], z0);
+    }
+    double r = b;   // r = b - G z0, all components
+#pragma unroll
+    for (int c = 0; c < K; ++c) r = fmad(-grow[c], g.from(z0, c), r);
+    double z = z0;
+    if (refine) {   // one step of iterative refinement on P
+      const double rp = inP ? r : 0.0;
+      double corr = 0.0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double rc = g.from(rp, c);
+        if (inP && ((P >> c) & 1u)) corr = fmad(A[c], rc, corr);
+      }
+      z = z0 + corr;
+    }
+    const uint32_t nonpos = g.bits(comp && inP && !dpos(z));
+    // a just-entered variable that does not come out positive is blocked
+    bool reject = false;
+    if (t_in >= 0) reject = (nonpos >> t_in) & 1u;
+    // Lawson-Hanson step (columns with nonpos != 0 and no rejection)
+    const bool stepping = !done && !reject && nonpos;
+    double yn = 0.0;
+    uint32_t drop = 0;
+    if (__any_sync(0xffffffffu, stepping)) {
+      const bool mine = stepping && ((nonpos >> g.a) & 1u);
+      double ratio = 2.0;
+      if (mine) {
+        ratio = y * rcp64(y - z);
+        if (!(dbits(ratio) >= 0)) ratio = 0.0;
+      }
+      double amin = ratio;
+#pragma unroll
+      for (int o = 1; o < KP; o <<= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, amin, o);
+        amin = dbits(w) < dbits(amin) ? w : amin;
+      }
+      const uint32_t atmin = g.bits(mine && dbits(ratio) == dbits(amin));
+      const double alpha = atmin ? amin : 0.0;
+      yn = (stepping && inP) ? fmad(alpha, z - y, y) : 0.0;
+      const int q = stepping ? __ffs(atmin ? atmin : nonpos) - 1 : 0;
+      drop = g.bits(stepping && comp && inP && !dpos(yn));
+      if (stepping) drop |= 1u << q;
+    }
+    // entering test (feasible columns): w = b - G y, the residual of the solve
+    const bool feas = !done && !reject && !nonpos;
+    const double yf = (feas && comp && inP) ? z : 0.0;
+    const double ymax = g.max_nn(yf);
+    const double tol = 10.0 * K * eps * (bmax + gmax * ymax);
+    const bool cand = feas && comp && !(((P | blocked) >> g.a) & 1u) && dgt_nn(r, tol);
+    const uint32_t cands = g.bits(cand);
+    double best = cand ? r : 0.0;
+#pragma unroll
+    for (int o = 1; o < KP; o <<= 1) best = dmax_nn(best, __shfl_xor_sync(0xffffffffu, best, o));
+    const uint32_t at = g.bits(cand && dbits(r) == dbits(best));
+    // apply the per-column transition
+    if (!done) {
+      if (reject) {
+        P &= ~(1u << t_in);
+        blocked |= 1u << t_in;
+        t_in = -1;
+      } else if (nonpos) {
+        t_in = -1;
+        y = ((drop >> g.a) & 1u) ? 0.0 : yn;
+        P &= ~drop;
+      } else {
+        t_in = -1;
+        y = yf;
+        if (!cands) {
+          status = 0;
+          done = true;
+        } else {
+          const int t = __ffs(at) - 1;
+          P |= 1u << t;
+          t_in = t;
+        }
+      }
+    }
+  }
+  *mask = g.bits(comp && dpos(y));
   return status;
 }
 

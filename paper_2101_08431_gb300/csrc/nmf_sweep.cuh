@@ -62,7 +62,8 @@ struct YSmem {
     double xch[2][8][Tr::VP];          // cluster exchange slots (C <= 8)
     double ybufD[2][Tr::TJ][K];
     typename AR::V ybufA[2][Tr::TJ][K];
-    double yt[Tr::TJ][NYT];            // per-column-lane KKT / objective terms
+    double yt[Tr::TJ][NYT];            // per-column-lane KKT / objective terms (k > 8)
+    double lt[32][NYT];                // per-lane KKT / objective terms (k <= 8)
     uint32_t samples[CACHE_N];
     InvCache<K> cache;                 // k > 8 only (no subset table)
     double gtab[(K <= 6) ? (1 << K) * K * K : 1];   // subset table of G, staged (k <= 6)
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(512, 1)
     }
     fence_mbar_init();
   }
+  for (int e = tid; e < TJ * NYT; e += Tr::T) (&sm.yt[0][0])[e] = 0.0;
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -279,8 +281,6 @@ __global__ void __launch_bounds__(512, 1)
       for (int e = lane; e < (1 << K) * K * K; e += 32) sm.gtab[e] = p.Gtab[e];
       for (int e = lane; e < (1 << K); e += 32) sm.gok[e] = p.Gok[e];
     }
-    if (lane < TJ)
-      for (int e = 0; e < NYT; ++e) sm.yt[lane][e] = 0.0;
     if (!TABLE) {
       if (lane < CACHE_N) {
         uint32_t msk = 0;
@@ -296,94 +296,191 @@ __global__ void __launch_bounds__(512, 1)
     NnlsSolver<K> solver;
     solver.init(sm.G, AR::EPS);
     if (!TABLE && mode == MODE_SWEEP) build_cache_warp<K>(&sm.cache, solver, sm.samples, CACHE_N);
-    double Ascr[K * K];
-    for (int t = 0; t < ntiles; ++t) {
-      const int slot = t & 1;
-      const int tj = min(TJ, ncols - t * TJ);
-      double yo[K], yn[K];
-      uint32_t old_mask = 0;
-      int phys = 0;
-      if (lane < tj) {   // warm start and passive set, fetched before B is ready
-        phys = wrap_col(p.head, c0 + t * TJ + lane, p.mcap);
+    double Ascr[K * K];   // scratch of the incremental solver (k > 8, degenerate entries)
+    if (TABLE) {
+      // lanes <-> (column slot jj, component a); per-lane KKT accumulators
+      LaneGroup<K> g;
+      g.init();
+      const int jj = lane / LaneGroup<K>::KP;
+      const bool ca = g.a < K;
+      double grow[K];
 #pragma unroll
-        for (int a = 0; a < K; ++a) yo[a] = p.Y[cur][(size_t)phys * K + a];
-        old_mask = p.ymask[cur][phys];
-      }
-      if (!mbar_wait(&sm.bready[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
+      for (int c = 0; c < K; ++c) grow[c] = ca ? sm.G[g.a * K + c] : 0.0;
+      double* acc_t = sm.lt[lane];
 #pragma unroll
-      for (int a = 0; a < K; ++a) yn[a] = 0.0;
-      if (lane < tj) {
-        double b[K];
-#pragma unroll
-        for (int a = 0; a < K; ++a) b[a] = sm.Bfull[slot][lane * K + a];
-        double* yt = sm.yt[lane];
-        if (mode != MODE_PRIME) {
-          // Y-half KKT terms of the incoming iterate: g = G y - b
-          double neg = 0.0, comp = 0.0, bn = 0.0, by = 0.0, ygy = 0.0, ymax = 0.0, yn2 = 0.0;
-#pragma unroll
-          for (int a = 0; a < K; ++a) {
-            const double g = dot_masked<K>(sm.G + a * K, yo, 0xffffffffu) - b[a];
-            const double mn = dminz(g), pos = dmaxz(g) * yo[a];
-            neg = fmad(mn, mn, neg);
-            comp = fmad(pos, pos, comp);
-            bn = fmad(b[a], b[a], bn);
-            by = fmad(b[a], yo[a], by);
-            ygy = fmad(yo[a], g + b[a], ygy);
-            ymax = dmax_nn(ymax, yo[a]);
-            yn2 = fmad(yo[a], yo[a], yn2);
-            if (!isfinite(b[a])) set_err(st, ERR_NONFINITE);
-          }
-          yt[YT_NEG] += neg;
-          yt[YT_COMP] += comp;
-          yt[YT_BNORM2] += bn;
-          yt[YT_BY] += by;
-          yt[YT_YGY] += ygy;
-          yt[YT_YMAX] = dmax_nn(yt[YT_YMAX], ymax);
-          yt[YT_YNORM2] += yn2;
+      for (int e = 0; e < NYT; ++e) acc_t[e] = 0.0;
+      const double* gtab = K <= 6 ? sm.gtab : p.Gtab;
+      const int* gok = K <= 6 ? sm.gok : p.Gok;
+      for (int t = 0; t < ntiles; ++t) {
+        const int slot = t & 1;
+        const int tj = min(TJ, ncols - t * TJ);
+        const bool active = jj < tj;
+        const bool comp = active && ca;
+        double yo = 0.0;
+        uint32_t old_mask = 0;
+        int phys = 0;
+        if (active) {   // warm start and passive set, fetched before B is ready
+          phys = wrap_col(p.head, c0 + t * TJ + jj, p.mcap);
+          if (ca) yo = p.Y[cur][(size_t)phys * K + g.a];
+          old_mask = p.ymask[cur][phys];
         }
-        if (mode == MODE_SWEEP) {
+        if (!mbar_wait(&sm.bready[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
+        const double b = comp ? sm.Bfull[slot][jj * K + g.a] : 0.0;
+        if (mode != MODE_PRIME) {
+          // Y-half KKT terms of the incoming iterate: g = G y - b (component a)
+          double gy = -b;
 #pragma unroll
-          for (int a = 0; a < K; ++a) yn[a] = yo[a];
-          uint32_t msk = 0;
-          int stt = -1;
-          if (TABLE)
-            stt = table_nnls<K>(solver, K <= 6 ? sm.gtab : p.Gtab, K <= 6 ? sm.gok : p.Gok, b, yn,
-                                p.warm != 0, &msk);
-          if (stt < 0) {
-#pragma unroll
-            for (int a = 0; a < K; ++a) yn[a] = yo[a];
-            stt = solver.solve(Ascr, b, yn, p.warm != 0, TABLE ? nullptr : &sm.cache, &msk);
+          for (int c = 0; c < K; ++c) gy = fmad(grow[c], g.from(yo, c), gy);
+          if (comp) {
+            const double mn = dminz(gy), pos = dmaxz(gy) * yo;
+            acc_t[YT_NEG] = fmad(mn, mn, acc_t[YT_NEG]);
+            acc_t[YT_COMP] = fmad(pos, pos, acc_t[YT_COMP]);
+            acc_t[YT_BNORM2] = fmad(b, b, acc_t[YT_BNORM2]);
+            acc_t[YT_BY] = fmad(b, yo, acc_t[YT_BY]);
+            acc_t[YT_YGY] = fmad(yo, gy + b, acc_t[YT_YGY]);
+            acc_t[YT_YMAX] = dmax_nn(acc_t[YT_YMAX], yo);
+            acc_t[YT_YNORM2] = fmad(yo, yo, acc_t[YT_YNORM2]);
+            if (!isfinite(b)) set_err(st, ERR_NONFINITE);
           }
-          double d2 = 0.0;
+        }
+        double yn = yo;
+        if (mode == MODE_SWEEP) {
+          uint32_t msk = 0;
+          int stt = lane_table_nnls<K>(g, gtab, gok, grow, solver.gmax, AR::EPS, b, yn, p.warm != 0,
+                                       active, AR::XD, &msk);
+          if (__any_sync(0xffffffffu, stt < 0)) {
+            // a degenerate table entry: the group's first lane solves the
+            // column with the incremental solver, then scatters the result
+            double bb[K], yy[K];
 #pragma unroll
-          for (int a = 0; a < K; ++a) d2 = fmad(yn[a] - yo[a], yn[a] - yo[a], d2);
-          yt[YT_DY2] += d2;
-          yt[YT_CHANGED] += (old_mask != msk) ? 1.0 : 0.0;
-          yt[YT_NOTCONV] += (double)stt;
-          if (crank == 0) {
+            for (int c = 0; c < K; ++c) {
+              bb[c] = g.from(b, c);
+              yy[c] = g.from(yo, c);
+            }
+            uint32_t m2 = 0;
+            int s2 = 0;
+            if (stt < 0 && g.a == 0) s2 = solver.solve(Ascr, bb, yy, p.warm != 0, nullptr, &m2);
 #pragma unroll
-            for (int a = 0; a < K; ++a) p.Y[nxt][(size_t)phys * K + a] = yn[a];
-            p.ymask[nxt][phys] = msk;
+            for (int c = 0; c < K; ++c) {
+              const double v = __shfl_sync(0xffffffffu, yy[c], g.base);
+              if (stt < 0 && g.a == c) yn = v;
+            }
+            const uint32_t mm = __shfl_sync(0xffffffffu, m2, g.base);
+            const int ss = __shfl_sync(0xffffffffu, s2, g.base);
+            if (stt < 0) {
+              msk = mm;
+              stt = ss;
+            }
+          }
+          if (comp) acc_t[YT_DY2] = fmad(yn - yo, yn - yo, acc_t[YT_DY2]);
+          if (active && g.a == 0) {
+            acc_t[YT_CHANGED] += (old_mask != msk) ? 1.0 : 0.0;
+            acc_t[YT_NOTCONV] += (double)stt;
+          }
+          if (crank == 0 && active) {
+            if (ca) p.Y[nxt][(size_t)phys * K + g.a] = yn;
+            if (g.a == 0) p.ymask[nxt][phys] = msk;
           }
         } else {
-          uint32_t msk = 0;
+          const uint32_t msk = g.bits(comp && dpos(yo));
+          if (mode == MODE_PRIME && crank == 0 && active && g.a == 0) p.ymask[cur][phys] = msk;
+        }
+        if (jj < TJ && ca) {
+          sm.ybufD[slot][jj][g.a] = active ? yn : 0.0;
+          sm.ybufA[slot][jj][g.a] = AR::yval(active ? yn : 0.0);
+        }
+        if (t == ntiles - 1) {
+          // the warp's terms (fixed lane order) into slot 0, before the last
+          // release: the compute warps read them in the epilogue
+#pragma unroll
+          for (int e = 0; e < NYT; ++e) {
+            const double v = (e == YT_YMAX) ? warp_max(acc_t[e]) : warp_sum(acc_t[e]);
+            if (lane == 0) sm.yt[0][e] = v;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.yready[slot]);
+      }
+    } else {
+      for (int t = 0; t < ntiles; ++t) {
+        const int slot = t & 1;
+        const int tj = min(TJ, ncols - t * TJ);
+        double yo[K], yn[K];
+        uint32_t old_mask = 0;
+        int phys = 0;
+        if (lane < tj) {   // warm start and passive set, fetched before B is ready
+          phys = wrap_col(p.head, c0 + t * TJ + lane, p.mcap);
+#pragma unroll
+          for (int a = 0; a < K; ++a) yo[a] = p.Y[cur][(size_t)phys * K + a];
+          old_mask = p.ymask[cur][phys];
+        }
+        if (!mbar_wait(&sm.bready[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
+#pragma unroll
+        for (int a = 0; a < K; ++a) yn[a] = 0.0;
+        if (lane < tj) {
+          double b[K];
+#pragma unroll
+          for (int a = 0; a < K; ++a) b[a] = sm.Bfull[slot][lane * K + a];
+          double* yt = sm.yt[lane];
+          if (mode != MODE_PRIME) {
+            double neg = 0.0, comp = 0.0, bn = 0.0, by = 0.0, ygy = 0.0, ymax = 0.0, yn2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+              const double gv = dot_masked<K>(sm.G + a * K, yo, 0xffffffffu) - b[a];
+              const double mn = dminz(gv), pos = dmaxz(gv) * yo[a];
+              neg = fmad(mn, mn, neg);
+              comp = fmad(pos, pos, comp);
+              bn = fmad(b[a], b[a], bn);
+              by = fmad(b[a], yo[a], by);
+              ygy = fmad(yo[a], gv + b[a], ygy);
+              ymax = dmax_nn(ymax, yo[a]);
+              yn2 = fmad(yo[a], yo[a], yn2);
+              if (!isfinite(b[a])) set_err(st, ERR_NONFINITE);
+            }
+            yt[YT_NEG] += neg;
+            yt[YT_COMP] += comp;
+            yt[YT_BNORM2] += bn;
+            yt[YT_BY] += by;
+            yt[YT_YGY] += ygy;
+            yt[YT_YMAX] = dmax_nn(yt[YT_YMAX], ymax);
+            yt[YT_YNORM2] += yn2;
+          }
+          if (mode == MODE_SWEEP) {
+#pragma unroll
+            for (int a = 0; a < K; ++a) yn[a] = yo[a];
+            uint32_t msk = 0;
+            const int stt = solver.solve(Ascr, b, yn, p.warm != 0, &sm.cache, &msk);
+            double d2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < K; ++a) d2 = fmad(yn[a] - yo[a], yn[a] - yo[a], d2);
+            yt[YT_DY2] += d2;
+            yt[YT_CHANGED] += (old_mask != msk) ? 1.0 : 0.0;
+            yt[YT_NOTCONV] += (double)stt;
+            if (crank == 0) {
+#pragma unroll
+              for (int a = 0; a < K; ++a) p.Y[nxt][(size_t)phys * K + a] = yn[a];
+              p.ymask[nxt][phys] = msk;
+            }
+          } else {
+            uint32_t msk = 0;
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+              yn[a] = yo[a];
+              if (dpos(yo[a])) msk |= 1u << a;
+            }
+            if (mode == MODE_PRIME && crank == 0) p.ymask[cur][phys] = msk;
+          }
+        }
+        if (lane < TJ) {
 #pragma unroll
           for (int a = 0; a < K; ++a) {
-            yn[a] = yo[a];
-            if (yo[a] > 0.0) msk |= 1u << a;
+            sm.ybufD[slot][lane][a] = yn[a];
+            sm.ybufA[slot][lane][a] = AR::yval(yn[a]);
           }
-          if (mode == MODE_PRIME && crank == 0) p.ymask[cur][phys] = msk;
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.yready[slot]);
       }
-      if (lane < TJ) {
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          sm.ybufD[slot][lane][a] = yn[a];
-          sm.ybufA[slot][lane][a] = AR::yval(yn[a]);
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.yready[slot]);
     }
   }
   if (timed_out) set_err(st, ERR_TIMEOUT);
@@ -546,7 +643,131 @@ __global__ void __launch_bounds__(XTraits<K>::T)
     else build_cache<K>(&cache, solver, samples, CACHE_N);
   }
 
-  if (warp == 0) {
+  if (TABLE) {
+    // lanes <-> (row slot jj, component a): warps 0 .. NWN-1 hold the 32 rows
+    constexpr int KP = LaneGroup<K>::KP, CPW = LaneGroup<K>::CPW, NWN = RB / CPW;
+    __shared__ double gram_w[NWN][K * K];
+    __shared__ double term_w[NWN][16];
+    if (warp < NWN) {
+      LaneGroup<K> g;
+      g.init();
+      const int jj = lane / KP;
+      const int lrow = warp * CPW + jj, grow_i = row0 + lrow;
+      const bool ract = grow_i < p.n;
+      const bool ca = g.a < K, comp = ract && ca;
+      double hrow[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) hrow[c] = ca ? H[g.a * K + c] : 0.0;
+      double pr = 0.0, xo = 0.0;
+      uint32_t old_mask = 0;
+      if (comp) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) pr += (double)psum[w][lrow][g.a];
+        xo = p.X[cur][(size_t)grow_i * K + g.a];
+      }
+      if (ract) old_mask = p.xmask[cur][grow_i];
+      double xn = xo;
+      uint32_t msk = 0;
+      int stt = 0;
+      if (mode == MODE_SWEEP) {
+        stt = lane_table_nnls<K>(g, tab, tok, hrow, solver.gmax, 2.220446049250313e-16, pr, xn,
+                                 p.warm != 0, ract, true, &msk);
+        if (__any_sync(0xffffffffu, stt < 0)) {
+          double bb[K], xx[K];
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            bb[c] = g.from(pr, c);
+            xx[c] = g.from(xo, c);
+          }
+          uint32_t m2 = 0;
+          int s2 = 0;
+          if (stt < 0 && g.a == 0) {
+            double Ascr[K * K];
+            s2 = solver.solve(Ascr, bb, xx, p.warm != 0, nullptr, &m2);
+          }
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            const double v = __shfl_sync(0xffffffffu, xx[c], g.base);
+            if (stt < 0 && g.a == c) xn = v;
+          }
+          const uint32_t mm = __shfl_sync(0xffffffffu, m2, g.base);
+          const int ss = __shfl_sync(0xffffffffu, s2, g.base);
+          if (stt < 0) {
+            msk = mm;
+            stt = ss;
+          }
+        }
+      } else {
+        msk = g.bits(comp && dpos(xo));
+      }
+      // X-half KKT terms of the iterate leaving this sweep: graX = H x - P
+      double gx = -pr;
+      double xc[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        xc[c] = g.from(xn, c);
+        gx = fmad(hrow[c], xc[c], gx);
+      }
+      double tv[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) tv[e] = 0.0;
+      if (comp) {
+        const double mn = dminz(gx), pos = dmaxz(gx) * xn;
+        tv[XT_NEG] = mn * mn;
+        tv[XT_COMP] = pos * pos;
+        tv[XT_PNORM2] = pr * pr;
+        tv[XT_XMAX] = xn;
+        tv[XT_XNORM2] = xn * xn;
+        tv[XT_DX2] = (xn - xo) * (xn - xo);
+        tv[XT_XP] = xn * pr;
+        if (!isfinite(pr)) set_err(st, ERR_NONFINITE);
+      }
+      if (ract && g.a == 0) {
+        tv[XT_CHANGED] = (mode == MODE_SWEEP && old_mask != msk) ? 1.0 : 0.0;
+        tv[XT_NOTCONV] = (double)stt;
+      }
+      // Gram partial: row a of x x^T summed over the warp's rows
+      double gr[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        double v = comp ? xn * xc[c] : 0.0;
+#pragma unroll
+        for (int o = KP; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        gr[c] = v;
+      }
+      if (lane < KP && ca) {
+#pragma unroll
+        for (int c = 0; c < K; ++c) gram_w[warp][g.a * K + c] = gr[c];
+      }
+      const double mx = warp_max(tv[XT_XMAX]);
+      tv[XT_XMAX] = 0.0;
+      const double tr = warp_reduce_scatter<16, double>(tv);
+      if (lane < 16) term_w[warp][lane] = (lane == XT_XMAX) ? mx : tr;
+      if (mode == MODE_SWEEP) {
+        if (comp) {
+          p.X[nxt][(size_t)grow_i * K + g.a] = xn;
+          p.X32[nxt][(size_t)grow_i * K + g.a] = (float)xn;
+        }
+        if (ract && g.a == 0) p.xmask[nxt][grow_i] = msk;
+      } else {
+        if (comp) p.X32[cur][(size_t)grow_i * K + g.a] = (float)xo;
+        if (ract && g.a == 0) p.xmask[cur][grow_i] = msk;
+      }
+    }
+    __syncthreads();
+    // block partial in fixed order over the warps
+    for (int e = tid; e < NV; e += T) {
+      double r = 0.0;
+      if (e < K * K) {
+        for (int w = 0; w < NWN; ++w) r += gram_w[w][e];
+      } else {
+        const int te = e - K * K;
+        for (int w = 0; w < NWN; ++w) r = (te == XT_XMAX) ? dmax_nn(r, term_w[w][te]) : r + term_w[w][te];
+      }
+      p.Xpart[(size_t)blockIdx.x * NV + e] = r;
+    }
+    __threadfence();
+  } else if (warp == 0) {
     double v[Tr::NVC * 32];
 #pragma unroll
     for (int e = 0; e < Tr::NVC * 32; ++e) v[e] = 0.0;
