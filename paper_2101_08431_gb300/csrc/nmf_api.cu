@@ -114,9 +114,9 @@ __global__ void kkt_stats_kernel(Problem p, int Q, double* out) {
     yfin[tid] = r;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < 32) {
     const int iter = st->iter;
-    combine_stats(yfin, st->xiter[iter & 1], st->msq, -1.0, iter, p.fp64_pass, out);
+    combine_stats_warp(yfin, st->xiter[iter & 1], st->msq, -1.0, iter, p.fp64_pass, out);
   }
 }
 
@@ -141,6 +141,7 @@ struct nmf_handle {
   void* dM = nullptr;
   double* dX[2] = {nullptr, nullptr};
   float* dX32[2] = {nullptr, nullptr};
+  float* dX32lo[2] = {nullptr, nullptr};
   double* dY[2] = {nullptr, nullptr};
   uint32_t* dYm[2] = {nullptr, nullptr};
   uint32_t* dXm[2] = {nullptr, nullptr};
@@ -214,13 +215,14 @@ bool make_plan(const nmf_handle* h, int var, YPlan* L) {
   const int cpc = (std::max(h->m, 1) + Q - 1) / Q;
   const int ntiles = (cpc + K.TJ - 1) / K.TJ;
   const size_t stage = (size_t)K.TJ * R * K.tm_size;
-  long long S = ((long long)h->smem_optin - (long long)K.small_bytes) / (long long)stage;
+  const size_t pacc = (size_t)R * K.pacc_row_bytes;
+  long long S = ((long long)h->smem_optin - (long long)K.small_bytes - (long long)pacc) / (long long)stage;
   if (S > 8) S = 8;
   if (S > ntiles) S = ntiles;
   // the pipeline refills the stage of tile t-1 while tile t is staged: two
   // stages at least whenever there is more than one tile
   if (S < (ntiles > 1 ? 2 : 1)) return false;
-  const size_t smem = K.small_bytes + (size_t)S * stage;
+  const size_t smem = K.small_bytes + (size_t)S * stage + pacc;
   // persistent grid: never more clusters than the device holds at once
   const int ci = C == 1 ? 0 : (C == 2 ? 1 : (C == 4 ? 2 : 3));
   const int fit = h->max_clusters[var][ci];
@@ -249,6 +251,7 @@ Problem make_problem(const nmf_handle* h, int var) {
   for (int b = 0; b < 2; ++b) {
     p.X[b] = h->dX[b];
     p.X32[b] = h->dX32[b];
+    p.X32lo[b] = h->dX32lo[b];
     p.Y[b] = h->dY[b];
     p.ymask[b] = h->dYm[b];
     p.xmask[b] = h->dXm[b];
@@ -398,7 +401,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
   for (int i = 0; i < nmf_handle::NEV; ++i)
     for (int j = 0; j < 3; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
-  void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dY[0], h->dY[1],
+  void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dX32lo[0], h->dX32lo[1], h->dY[0], h->dY[1],
                    h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage};
@@ -472,6 +475,7 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   for (int b = 0; b < 2; ++b) {
     ok &= dalloc(&h->dX[b], nk) == cudaSuccess;
     ok &= dalloc(&h->dX32[b], nk) == cudaSuccess;
+    ok &= dalloc(&h->dX32lo[b], nk) == cudaSuccess;
     ok &= dalloc(&h->dY[b], mk) == cudaSuccess;
     ok &= dalloc(&h->dYm[b], h->mcap) == cudaSuccess;
     ok &= dalloc(&h->dXm[b], h->n) == cudaSuccess;

@@ -15,17 +15,63 @@
 //           carry ~44 significant bits.
 //
 // Every policy provides: V (staged factor value), A (accumulator), P (type
-// of the stored P partials), xval / yval (staging from FP64), zero, madd,
-// add, shfl_xor, to_double, to_p, and EPS (the epsilon of the NNLS entering
-// tolerance for sweeps computed with this policy).
+// of the stored P partials), R (type of the cross-warp and cross-CTA sums of
+// B: FP32 instructions only where the pass itself avoids FP64), load_x /
+// yval (staging of X from its stored copies, of y from FP64), zero, vzero,
+// madd, add, shfl_xor, to_double, to_p, to_r, radd, rshfl_xor, r_to_double,
+// and EPS (the epsilon of the NNLS entering tolerance for sweeps computed
+// with this policy).
 #pragma once
 
 #include "nmf_common.cuh"
 
 namespace nmfgb {
 
-struct DF {
+struct alignas(8) DF {
   float hi, lo;
+};
+
+// Double-float addition (Knuth's TwoSum of the high words, then the low
+// words, renormalised): the cross-warp and cross-CTA reduction type of the
+// FP32 and compensated passes (FP32 instructions only).
+__device__ __forceinline__ float df_two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  err = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+  return s;
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float err;
+  const float s = df_two_sum(a.hi, b.hi, err);
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+  const float h = __fadd_rn(s, lo);
+  return {h, __fadd_rn(lo, -__fadd_rn(h, -s))};
+}
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// Arithmetic on the stored partials of P = M Y^T (the row pass sums the
+// cluster partials in their own type and converts once).
+template <typename T>
+struct PartOps;
+template <>
+struct PartOps<float> {
+  __device__ static float zero() { return 0.f; }
+  __device__ static float add(float a, float b) { return a + b; }
+  __device__ static double to_double(float a) { return (double)a; }
+};
+template <>
+struct PartOps<double> {
+  __device__ static double zero() { return 0.0; }
+  __device__ static double add(double a, double b) { return a + b; }
+  __device__ static double to_double(double a) { return a; }
+};
+template <>
+struct PartOps<DF> {
+  __device__ static DF zero() { return {0.f, 0.f}; }
+  __device__ static DF add(DF a, DF b) { return df_add(a, b); }
+  __device__ static double to_double(DF a) { return (double)a.hi + (double)a.lo; }
 };
 
 struct ArF32 {
@@ -33,8 +79,15 @@ struct ArF32 {
   using A = float;
   using P = float;
   static constexpr bool XD = false;   // X is staged from its FP32 copy
+  static constexpr bool PACC_SMEM = false;   // P accumulators in registers
   static constexpr double EPS = 1.1920928955078125e-07;
-  __device__ static V xval(double, float x32) { return x32; }
+  using R = DF;   // cross-warp / cross-CTA reduction of B
+  __device__ static V load_x(const Problem& p, int b, size_t i) { return p.X32[b][i]; }
+  __device__ static V vzero() { return 0.f; }
+  __device__ static R to_r(A a) { return {a, 0.f}; }
+  __device__ static R radd(R a, R b) { return df_add(a, b); }
+  __device__ static R rshfl_xor(R a, int o) { return df_shfl_xor(a, o); }
+  __device__ static double r_to_double(R a) { return (double)a.hi + (double)a.lo; }
   __device__ static V yval(double y) { return (float)y; }
   __device__ static A zero() { return 0.f; }
   template <typename TM>
@@ -50,8 +103,15 @@ struct ArF64 {
   using A = double;
   using P = double;
   static constexpr bool XD = true;
+  static constexpr bool PACC_SMEM = false;
   static constexpr double EPS = 2.220446049250313e-16;
-  __device__ static V xval(double x, float) { return x; }
+  using R = double;
+  __device__ static V load_x(const Problem& p, int b, size_t i) { return p.X[b][i]; }
+  __device__ static V vzero() { return 0.0; }
+  __device__ static R to_r(A a) { return a; }
+  __device__ static R radd(R a, R b) { return __dadd_rn(a, b); }
+  __device__ static R rshfl_xor(R a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static double r_to_double(R a) { return a; }
   __device__ static V yval(double y) { return y; }
   __device__ static A zero() { return 0.0; }
   template <typename TM>
@@ -65,23 +125,28 @@ struct ArF64 {
 struct ArDF {
   using V = DF;
   using A = DF;
-  using P = double;
+  using P = DF;   // partials stay double-float: no FP64 instruction in the epilogue
   static constexpr bool XD = true;
   static constexpr double EPS = 5.684341886080802e-14;   // 2^-44
+  // the P accumulators (two words each) live in shared memory, so that a
+  // CTA holds as many rows as in the FP32 pass (no cluster exchange)
+  static constexpr bool PACC_SMEM = true;
   __device__ static V split(double x) {
     const float hi = __double2float_rn(x);
     return {hi, __double2float_rn(x - (double)hi)};
   }
-  __device__ static V xval(double x, float) { return split(x); }
+  using R = DF;
+  // the split of X is formed by the row pass that produced it (X32, X32lo)
+  __device__ static V load_x(const Problem& p, int b, size_t i) { return {p.X32[b][i], p.X32lo[b][i]}; }
+  __device__ static V vzero() { return {0.f, 0.f}; }
+  __device__ static R to_r(A a) { return a; }
+  __device__ static R radd(R a, R b) { return df_add(a, b); }
+  __device__ static R rshfl_xor(R a, int o) { return df_shfl_xor(a, o); }
+  __device__ static double r_to_double(R a) { return (double)a.hi + (double)a.lo; }
   __device__ static V yval(double y) { return split(y); }
   __device__ static A zero() { return {0.f, 0.f}; }
   // Knuth's TwoSum: s + err == a + b exactly.
-  __device__ static float two_sum(float a, float b, float& err) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fadd_rn(s, -a);
-    err = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
-    return s;
-  }
+  __device__ static float two_sum(float a, float b, float& err) { return df_two_sum(a, b, err); }
   __device__ static A madd(float m, V v, A a) {
     const float p = __fmul_rn(m, v.hi);
     const float e = __fmaf_rn(m, v.hi, -p);            // m * v.hi == p + e exactly
@@ -89,18 +154,10 @@ struct ArDF {
     const float s = two_sum(a.hi, p, err);
     return {s, __fadd_rn(a.lo, __fadd_rn(err, __fmaf_rn(m, v.lo, e)))};
   }
-  __device__ static A add(A a, A b) {
-    float err;
-    const float s = two_sum(a.hi, b.hi, err);
-    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
-    const float h = __fadd_rn(s, lo);                   // renormalise (|s| >= |lo|)
-    return {h, __fadd_rn(lo, -__fadd_rn(h, -s))};
-  }
-  __device__ static A shfl_xor(A a, int o) {
-    return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-  }
+  __device__ static A add(A a, A b) { return df_add(a, b); }
+  __device__ static A shfl_xor(A a, int o) { return df_shfl_xor(a, o); }
   __device__ static double to_double(A a) { return (double)a.hi + (double)a.lo; }
-  __device__ static P to_p(A a) { return to_double(a); }
+  __device__ static P to_p(A a) { return a; }
 };
 
 // Reduce-scatter of VP = 2^p <= 32 accumulators held by every lane: lane l

@@ -59,6 +59,7 @@ struct Problem {
   const void* M;          // ld x mcap, column-major, float or double
   double* X[2];           // n x k row-major, FP64
   float* X32[2];          // FP32 copy of X
+  float* X32lo[2];        // fl32(x - fl32(x)): low word of X for the compensated pass
   double* Y[2];           // k x mcap column-major (physical column order), FP64
   uint32_t* ymask[2];     // passive set of each column
   uint32_t* xmask[2];     // passive set of each row

@@ -3,5 +3,5 @@
 #include "nmf_launch.cuh"
 
 namespace nmfgb {
-bool get_kernels_df(int k, KernelSet* out) { NMF_FILL_ALL(float, ArDF, double) }
+bool get_kernels_df(int k, KernelSet* out) { NMF_FILL_ALL(float, ArDF, DF) }
 }  // namespace nmfgb

@@ -27,6 +27,7 @@ struct KernelSet {
   int rows;                                  // rows one CTA of the M pass can own
   size_t small_bytes;
   int tm_size;
+  int pacc_row_bytes;                        // shared-memory P accumulators per owned row
 };
 
 bool get_kernels_f32(int k, KernelSet* out);
@@ -118,6 +119,7 @@ cudaError_t launch_x(const Problem& p, int mode, int Q, int nxblk, cudaStream_t 
     out->rows = YTraits<TM, AR, K>::ROWS;                    \
     out->small_bytes = YSmem<TM, AR, K>::small_bytes();      \
     out->tm_size = (int)sizeof(TM);                          \
+    out->pacc_row_bytes = YTraits<TM, AR, K>::PACC_ROW_BYTES; \
     return true;
 
 #define NMF_FILL_ALL(TM, AR, PT)                                                                  \

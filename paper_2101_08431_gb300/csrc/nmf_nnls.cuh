@@ -486,6 +486,91 @@ struct LaneGroup {
   }
 };
 
+// The subset table built level by level by lane groups: in level L every
+// group of KP lanes takes one subset P with L elements and borders
+// inv(G_{P-h}) (h the highest index of P) into inv(G_PP), lane a computing
+// row a.  The arithmetic is that of NnlsSolver::add in the same order, so
+// the entries equal those of build_subset_table; entries outside P are 0.
+// The subsets of a level are enumerated in increasing order from warp
+// ballots (no table in memory: after an L2 flush a memory lookup would wait
+// behind the TMA stream of M).  Called by the `nthreads` threads starting at
+// thread t0 (both multiples of 32); sync() must be a barrier over exactly
+// those threads.  Warps without a subset in a round skip its arithmetic.
+template <int K, typename Sync>
+__device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, int* ok, int t0, int nthreads,
+                                         Sync sync) {
+  static_assert(K <= 8, "subset tables are built for k <= 8");
+  constexpr int KP = LaneGroup<K>::KP, CPW = LaneGroup<K>::CPW;
+  constexpr int NC = (1 << K) - 1;              // candidate subsets 1 .. 2^K - 1
+  constexpr int NB = (NC + 31) / 32;            // ballot words
+  LaneGroup<K> g;
+  g.init();
+  const int local = (int)threadIdx.x - t0;
+  const int group = local / KP, ngroups = nthreads / KP;
+  const int wgroup = (local >> 5) * CPW;        // first group of this warp
+  if (local == 0) ok[0] = 1;
+#pragma unroll 1
+  for (int L = 1; L <= K; ++L) {
+    uint32_t words[NB];
+    int ntask = 0;
+#pragma unroll
+    for (int w = 0; w < NB; ++w) {
+      const int v = w * 32 + g.lane + 1;
+      words[w] = __ballot_sync(0xffffffffu, v <= NC && __popc(v) == L);
+      ntask += __popc(words[w]);
+    }
+#pragma unroll 1
+    for (int base = 0; base < ntask; base += ngroups) {
+      if (base + wgroup >= ntask) continue;     // warp-uniform
+      const int task = base + group;
+      const bool valid = task < ntask;
+      uint32_t P = 1u;
+      if (valid) {
+        int r = task;
+#pragma unroll
+        for (int w = 0; w < NB; ++w) {
+          const int c = __popc(words[w]);
+          if (r >= 0 && r < c) P = (uint32_t)(w * 32 + 1 + (int)__fns(words[w], 0, r + 1));
+          r -= c;
+        }
+      }
+      const int h = 31 - __clz(P);
+      const uint32_t par = P & ~(1u << h);
+      const double* A = tab + (size_t)par * K * K;
+      double gi[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) gi[c] = S.G[c * K + h];
+      const bool ina = g.a < K && ((par >> g.a) & 1u);
+      const double u = ina ? dot_masked<K>(A + g.a * K, gi, par) : 0.0;
+      double t = ina ? S.G[h * K + g.a] * u : 0.0;
+#pragma unroll
+      for (int o = 1; o < KP; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const double sp = S.G[h * K + h] - t;
+      const bool good = valid && (par == 0 || ok[par] != 0) && (sp > S.pivot_min);
+      const double rs = rcp64(sp);
+      const double ua = u * rs;
+      double* D = tab + (size_t)P * K * K + g.a * K;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double uc = g.from(u, c);
+        if (valid && g.a < K) {
+          double v = 0.0;
+          if (ina) {
+            if ((par >> c) & 1u) v = fmad(ua, uc, A[g.a * K + c]);
+            else if (c == h) v = -ua;
+          } else if (g.a == h) {
+            if ((par >> c) & 1u) v = -(uc * rs);
+            else if (c == h) v = rs;
+          }
+          D[c] = v;
+        }
+      }
+      if (valid && g.a == 0) ok[P] = good ? 1 : 0;
+    }
+    sync();
+  }
+}
+
 // Solve the columns held by the warp.  Per lane: b = component a of the
 // right-hand side, y = component a of the warm start (in) / solution (out),
 // grow = row a of G (K values, registers).  tab / ok: subset table of G.

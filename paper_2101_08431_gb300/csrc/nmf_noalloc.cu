@@ -112,11 +112,12 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   const int cpc = (int)((m + L.Q - 1) / L.Q);
   const int ntiles = (cpc + ks.TJ - 1) / ks.TJ;
   const size_t stage = (size_t)ks.TJ * R * sizeof(float);
-  long long S = ((long long)optin - (long long)ks.small_bytes) / (long long)stage;
+  const size_t pacc = (size_t)R * ks.pacc_row_bytes;
+  long long S = ((long long)optin - (long long)ks.small_bytes - (long long)pacc) / (long long)stage;
   S = std::min<long long>(std::min<long long>(S, 8), ntiles);
   if (S < (ntiles > 1 ? 2 : 1)) return NMF_ECAPACITY;
   L.S = (int)S;
-  L.smem = ks.small_bytes + (size_t)S * stage;
+  L.smem = ks.small_bytes + (size_t)S * stage + pacc;
 
   // carve the scratch
   unsigned char* b = static_cast<unsigned char*>(base);
@@ -129,6 +130,8 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   double* Xn = reinterpret_cast<double*>(b + take(off, sizeof(double) * NA_NMAX * NA_KMAX));
   float* X32a = reinterpret_cast<float*>(b + take(off, sizeof(float) * NA_NMAX * NA_KMAX));
   float* X32b = reinterpret_cast<float*>(b + take(off, sizeof(float) * NA_NMAX * NA_KMAX));
+  float* X32la = reinterpret_cast<float*>(b + take(off, sizeof(float) * NA_NMAX * NA_KMAX));
+  float* X32lb = reinterpret_cast<float*>(b + take(off, sizeof(float) * NA_NMAX * NA_KMAX));
   double* Yn = reinterpret_cast<double*>(b + take(off, sizeof(double) * NA_MMAX * NA_KMAX));
   uint32_t* ym0 = reinterpret_cast<uint32_t*>(b + take(off, sizeof(uint32_t) * NA_MMAX));
   uint32_t* ym1 = reinterpret_cast<uint32_t*>(b + take(off, sizeof(uint32_t) * NA_MMAX));
@@ -154,6 +157,8 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   p.X[1] = Xn;
   p.X32[0] = X32a;
   p.X32[1] = X32b;
+  p.X32lo[0] = X32la;
+  p.X32lo[1] = X32lb;
   p.Y[0] = Y;
   p.Y[1] = Yn;
   p.ymask[0] = ym0;

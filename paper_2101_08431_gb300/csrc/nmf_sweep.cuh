@@ -29,10 +29,13 @@ namespace nmfgb {
 template <typename TM, typename AR, int K>
 struct YTraits {
   static constexpr bool WIDE = sizeof(typename AR::V) == 8;   // 8-byte staged factors
+  static constexpr bool PSM = AR::PACC_SMEM;                   // P accumulators in shared memory
   static constexpr int T = 512;
   static constexpr int NCW = 15;                               // compute warps
   static constexpr int TC = NCW * 32;                          // compute threads
-  static constexpr int RPT = WIDE ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 7 : (K <= 8 ? 4 : 2));
+  static constexpr int RPT = (WIDE && !PSM) ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 7 : (K <= 8 ? 4 : 2));
+  // shared-memory bytes of the P accumulators per owned row (PSM only)
+  static constexpr int PACC_ROW_BYTES = PSM ? K * (int)sizeof(typename AR::A) : 0;
   static constexpr int TJ = WIDE ? (K <= 4 ? 4 : (K <= 8 ? 2 : 1)) : (K <= 4 ? 8 : (K <= 8 ? 4 : 2));
   static constexpr int V = TJ * K;
   static constexpr int VP = (V <= 1) ? 1 : (V <= 2) ? 2 : (V <= 4) ? 4 : (V <= 8) ? 8 : (V <= 16) ? 16 : 32;
@@ -58,8 +61,8 @@ struct YSmem {
     double Hacc[K * K];
     double Bfull[2][Tr::VP];
     double Bpart[Tr::VP];
-    double red[Tr::NCW][Tr::VP];
-    double xch[2][8][Tr::VP];          // cluster exchange slots (C <= 8)
+    typename AR::R red[Tr::NCW][Tr::VP];
+    typename AR::R xch[2][8][Tr::VP];  // cluster exchange slots (C <= 8)
     double ybufD[2][Tr::TJ][K];
     typename AR::V ybufA[2][Tr::TJ][K];
     double yt[Tr::TJ][NYT];            // per-column-lane KKT / objective terms (k > 8)
@@ -113,6 +116,7 @@ __global__ void __launch_bounds__(512, 1)
     fence_mbar_init();
   }
   for (int e = tid; e < TJ * NYT; e += Tr::T) (&sm.yt[0][0])[e] = 0.0;
+  for (int e = tid; e < K * K; e += Tr::T) sm.Hacc[e] = 0.0;
   if (C > 1) cluster.sync();
   else __syncthreads();
 
@@ -134,23 +138,23 @@ __global__ void __launch_bounds__(512, 1)
     // ======================= compute warps ==================================
     if (tid == 0)
       for (int t = 0; t < min(S, ntiles); ++t) issue(t, t);
-    if (tid < K * K) sm.Hacc[tid] = 0.0;
     VT xr[RPT][K];
-    AT pacc[RPT][K];
+    constexpr bool PSM = Tr::PSM;
+    AT pacc[PSM ? 1 : RPT][K];
+    // PSM: accumulators component-major behind the stages, ps[a * R + rr]
+    AT* ps = reinterpret_cast<AT*>(smem_raw + Sm::small_bytes() + (size_t)S * Sm::stage_bytes(R));
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       const int row = r0 + tid + r * TC;
       const bool ok = (tid + r * TC) < rows_c && row < p.n;
 #pragma unroll
       for (int a = 0; a < K; ++a) {
-        double xd = 0.0;
-        float xf = 0.f;
-        if (ok) {
-          if (AR::XD) xd = p.X[cur][(size_t)row * K + a];
-          else xf = p.X32[cur][(size_t)row * K + a];
+        xr[r][a] = ok ? AR::load_x(p, cur, (size_t)row * K + a) : AR::vzero();
+        if constexpr (PSM) {
+          if (tid + r * TC < R) ps[(size_t)a * R + tid + r * TC] = AR::zero();
+        } else {
+          pacc[r][a] = AR::zero();
         }
-        xr[r][a] = AR::xval(xd, xf);
-        pacc[r][a] = AR::zero();
       }
     }
     // Iteration t contracts tile t (t < ntiles) and then accumulates tile
@@ -180,37 +184,40 @@ __global__ void __launch_bounds__(512, 1)
         }
         {
           const AT wsum = warp_reduce_scatter_ar<AR, VP>(acc);
-          if (lane < VP) sm.red[warp][lane] = AR::to_double(wsum);
+          if (lane < VP) sm.red[warp][lane] = AR::to_r(wsum);
         }
         named_sync(1, TC);
-        if (tid < ((4 * VP + 31) & ~31)) {      // 4 lanes per value, then a quad tree
+        // 4 lanes per value, then a quad tree; sums in the pass's reduction
+        // type R (double-float for the FP32 passes: no FP64 instruction here)
+        using RT = typename AR::R;
+        if (tid < ((4 * VP + 31) & ~31)) {
           const int v = tid >> 2, g = tid & 3;
-          double bs = 0.0;
+          RT bs = AR::to_r(AR::zero());
           if (v < VP) {
 #pragma unroll
-            for (int w = g; w < NCW; w += 4) bs += sm.red[w][v];
+            for (int w = g; w < NCW; w += 4) bs = AR::radd(bs, sm.red[w][v]);
           }
-          bs += __shfl_xor_sync(0xffffffffu, bs, 1);
-          bs += __shfl_xor_sync(0xffffffffu, bs, 2);
+          bs = AR::radd(bs, AR::rshfl_xor(bs, 1));
+          bs = AR::radd(bs, AR::rshfl_xor(bs, 2));
           if (g == 0 && v < VP) {
             if (C > 1) {
               // push this CTA's partial to every CTA of the cluster
               for (int rk = 0; rk < C; ++rk) {
-                double* dst = cluster.map_shared_rank(&sm.xch[slot][crank][v], rk);
+                RT* dst = cluster.map_shared_rank(&sm.xch[slot][crank][v], rk);
                 *dst = bs;
                 mbar_arrive_remote(&sm.xbar[slot], (uint32_t)rk);
               }
             } else {
-              sm.Bfull[slot][v] = bs;
+              sm.Bfull[slot][v] = AR::r_to_double(bs);
             }
           }
         }
         if (C > 1) {
           if (!mbar_wait_cluster(&sm.xbar[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
           if (tid < VP) {
-            double bs = 0.0;
-            for (int c = 0; c < C; ++c) bs += sm.xch[slot][c][tid];
-            sm.Bfull[slot][tid] = bs;
+            RT bs = sm.xch[slot][0][tid];
+            for (int c = 1; c < C; ++c) bs = AR::radd(bs, sm.xch[slot][c][tid]);
+            sm.Bfull[slot][tid] = AR::r_to_double(bs);
           }
         }
         named_sync(1, TC);
@@ -226,17 +233,26 @@ __global__ void __launch_bounds__(512, 1)
           for (int r = 0; r < RPT; ++r) {
             const int rr = tid + r * TC;
             if (rr < rows_c) {
+              AT pa[K];
+#pragma unroll
+              for (int a = 0; a < K; ++a) pa[a] = PSM ? ps[(size_t)a * R + rr] : pacc[PSM ? 0 : r][a];
 #pragma unroll
               for (int jj = 0; jj < TJ; ++jj) {
                 if (jj < tj) {
                   const TM mv = tile[(size_t)jj * R + rr];
 #pragma unroll
-                  for (int a = 0; a < K; ++a) pacc[r][a] = AR::madd(mv, sm.ybufA[ub][jj][a], pacc[r][a]);
+                  for (int a = 0; a < K; ++a) pa[a] = AR::madd(mv, sm.ybufA[ub][jj][a], pa[a]);
                 }
+              }
+#pragma unroll
+              for (int a = 0; a < K; ++a) {
+                if constexpr (PSM) ps[(size_t)a * R + rr] = pa[a];
+                else pacc[PSM ? 0 : r][a] = pa[a];
               }
             }
           }
-          if (tid >= 32 && tid < 32 + K * K) {     // pairwise tree over the tile's columns
+          if (!TABLE && tid >= 32 && tid < 32 + K * K) {   // k > 8: pairwise tree over the tile's columns
+            // (k <= 8: H is accumulated by the NNLS warp)
             const int e = tid - 32, a = e / K, c = e % K;
             double hp[TJ];
 #pragma unroll
@@ -262,7 +278,9 @@ __global__ void __launch_bounds__(512, 1)
         const int row = r0 + rr;
         if (rr < rows_c && row < p.n) {
 #pragma unroll
-          for (int a = 0; a < K; ++a) Pp[((size_t)q * p.ld + row) * K + a] = AR::to_p(pacc[r][a]);
+          for (int a = 0; a < K; ++a)
+            Pp[((size_t)q * p.ld + row) * K + a] =
+                AR::to_p(PSM ? ps[(size_t)a * R + rr] : pacc[PSM ? 0 : r][a]);
         }
       }
     }
@@ -277,10 +295,6 @@ __global__ void __launch_bounds__(512, 1)
   } else {
     // ======================= NNLS warp ======================================
     for (int e = lane; e < K * K; e += 32) sm.G[e] = p.G[e];
-    if (K <= 6 && mode == MODE_SWEEP) {
-      for (int e = lane; e < (1 << K) * K * K; e += 32) sm.gtab[e] = p.Gtab[e];
-      for (int e = lane; e < (1 << K); e += 32) sm.gok[e] = p.Gok[e];
-    }
     if (!TABLE) {
       if (lane < CACHE_N) {
         uint32_t msk = 0;
@@ -296,6 +310,8 @@ __global__ void __launch_bounds__(512, 1)
     NnlsSolver<K> solver;
     solver.init(sm.G, AR::EPS);
     if (!TABLE && mode == MODE_SWEEP) build_cache_warp<K>(&sm.cache, solver, sm.samples, CACHE_N);
+    // k <= 6: the subset table of G is built below by this warp while the
+    // compute warps contract the first tile (k = 7, 8: by the previous row pass)
     double Ascr[K * K];   // scratch of the incremental solver (k > 8, degenerate entries)
     if (TABLE) {
       // lanes <-> (column slot jj, component a); per-lane KKT accumulators
@@ -309,20 +325,39 @@ __global__ void __launch_bounds__(512, 1)
       double* acc_t = sm.lt[lane];
 #pragma unroll
       for (int e = 0; e < NYT; ++e) acc_t[e] = 0.0;
+      double hacc[K];   // row a of H = Y Y^T over this warp's column slots
+#pragma unroll
+      for (int c = 0; c < K; ++c) hacc[c] = 0.0;
       const double* gtab = K <= 6 ? sm.gtab : p.Gtab;
       const int* gok = K <= 6 ? sm.gok : p.Gok;
+      // warm start and passive set of the next tile, fetched one tile ahead
+      double yo_nx = 0.0;
+      uint32_t om_nx = 0;
+      int ph_nx = 0;
+      if (jj < min(TJ, ncols)) {
+        ph_nx = wrap_col(p.head, c0 + jj, p.mcap);
+        if (ca) yo_nx = p.Y[cur][(size_t)ph_nx * K + g.a];
+        om_nx = p.ymask[cur][ph_nx];
+      }
+      if constexpr (K <= 6) {
+        if (mode == MODE_SWEEP)
+          build_subset_table_lanes<K>(solver, sm.gtab, sm.gok, NCW * 32, 32, [] { __syncwarp(); });
+      }
       for (int t = 0; t < ntiles; ++t) {
         const int slot = t & 1;
         const int tj = min(TJ, ncols - t * TJ);
         const bool active = jj < tj;
         const bool comp = active && ca;
-        double yo = 0.0;
-        uint32_t old_mask = 0;
-        int phys = 0;
-        if (active) {   // warm start and passive set, fetched before B is ready
-          phys = wrap_col(p.head, c0 + t * TJ + jj, p.mcap);
-          if (ca) yo = p.Y[cur][(size_t)phys * K + g.a];
-          old_mask = p.ymask[cur][phys];
+        const double yo = yo_nx;
+        const uint32_t old_mask = om_nx;
+        const int phys = ph_nx;
+        yo_nx = 0.0;
+        om_nx = 0;
+        ph_nx = 0;
+        if (t + 1 < ntiles && jj < min(TJ, ncols - (t + 1) * TJ)) {
+          ph_nx = wrap_col(p.head, c0 + (t + 1) * TJ + jj, p.mcap);
+          if (ca) yo_nx = p.Y[cur][(size_t)ph_nx * K + g.a];
+          om_nx = p.ymask[cur][ph_nx];
         }
         if (!mbar_wait(&sm.bready[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
         const double b = comp ? sm.Bfull[slot][jj * K + g.a] : 0.0;
@@ -385,11 +420,26 @@ __global__ void __launch_bounds__(512, 1)
           const uint32_t msk = g.bits(comp && dpos(yo));
           if (mode == MODE_PRIME && crank == 0 && active && g.a == 0) p.ymask[cur][phys] = msk;
         }
+        if (mode != MODE_KKT) {
+          const double yv = comp ? yn : 0.0;
+#pragma unroll
+          for (int c = 0; c < K; ++c) hacc[c] = fmad(yv, g.from(yv, c), hacc[c]);
+        }
         if (jj < TJ && ca) {
           sm.ybufD[slot][jj][g.a] = active ? yn : 0.0;
           sm.ybufA[slot][jj][g.a] = AR::yval(active ? yn : 0.0);
         }
         if (t == ntiles - 1) {
+          // H over the column slots (fixed butterfly order), into Hacc
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+#pragma unroll
+            for (int o = LaneGroup<K>::KP; o < 32; o <<= 1) hacc[c] += __shfl_xor_sync(0xffffffffu, hacc[c], o);
+          }
+          if (lane < LaneGroup<K>::KP && ca) {
+#pragma unroll
+            for (int c = 0; c < K; ++c) sm.Hacc[g.a * K + c] = hacc[c];
+          }
           // the warp's terms (fixed lane order) into slot 0, before the last
           // release: the compute warps read them in the epilogue
 #pragma unroll
@@ -488,27 +538,43 @@ __global__ void __launch_bounds__(512, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Combine the terms of iterate t into its statistics record (Sec. 5.1 KKT
-// error with r = max(graX, 0), s = max(graY, 0), 2-norms; f from the Grams).
+// Statistics record of iterate t (Sec. 5.1 KKT error with r = max(graX, 0),
+// s = max(graY, 0), 2-norms; f from the Grams) from the Y-half terms (this
+// sweep's M pass) and the X-half terms (the row pass that produced X_t).
 // ---------------------------------------------------------------------------
-__device__ inline void combine_stats(const double* yterm, const double* xterm, double msq,
-                                     double dx2, int iter, int fp64, double* out) {
+// Called by the 32 lanes of one warp: the six square roots and three quotients run on
+// separate lanes (each FP64 warp instruction costs the same whatever the
+// number of active lanes); lane 0 writes out[].  dx2 < 0: no step term.
+__device__ inline void combine_stats_warp(const double* yterm, const double* xterm, double msq,
+                                          double dx2, int iter, int fp64, double* out) {
+  const int lane = threadIdx.x & 31;
   const double neg = yterm[YT_NEG] + xterm[XT_NEG];
   const double comp = yterm[YT_COMP] + xterm[XT_COMP];
-  const double sg = sqrt(xterm[XT_PNORM2]) + sqrt(yterm[YT_BNORM2]);
+  double arg = 0.0;
+  if (lane == 0) arg = neg;
+  else if (lane == 1) arg = comp;
+  else if (lane == 2) arg = xterm[XT_PNORM2];
+  else if (lane == 3) arg = yterm[YT_BNORM2];
+  else if (lane == 4) arg = dx2 >= 0.0 ? dx2 + yterm[YT_DY2] : 0.0;
+  else if (lane == 5) arg = xterm[XT_XNORM2] + yterm[YT_YNORM2];
+  const double sq = sqrt(arg);
+  const double e1 = __shfl_sync(0xffffffffu, sq, 0), e2 = __shfl_sync(0xffffffffu, sq, 1);
+  const double sg = __shfl_sync(0xffffffffu, sq, 2) + __shfl_sync(0xffffffffu, sq, 3);
+  const double s4 = __shfl_sync(0xffffffffu, sq, 4), s5 = __shfl_sync(0xffffffffu, sq, 5);
   const double xymax = fmax(xterm[XT_XMAX], yterm[YT_YMAX]);
-  const double e1 = sqrt(neg), e2 = sqrt(comp);
-  const double r1 = sg > 0.0 ? e1 / sg : e1;
   const double d2 = sg * xymax;
-  const double r2 = d2 > 0.0 ? e2 / d2 : e2;
+  const double num = lane == 0 ? e1 : (lane == 1 ? e2 : s4);
+  const double den = lane == 0 ? sg : (lane == 1 ? d2 : 1.0 + s5);
+  const double qt = (lane >= 2 || den > 0.0) ? num / den : num;
+  const double r1 = __shfl_sync(0xffffffffu, qt, 0), r2 = __shfl_sync(0xffffffffu, qt, 1);
+  const double step = __shfl_sync(0xffffffffu, qt, 2);
+  if (lane != 0) return;
   for (int e = 0; e < NSTAT; ++e) out[e] = 0.0;
   out[ST_ITER] = iter;
   out[ST_F] = 0.5 * (msq - 2.0 * yterm[YT_BY] + yterm[YT_YGY]);
   out[ST_EABS] = fmax(e1, e2);
   out[ST_REL] = fmax(r1, r2);
-  out[ST_STEP] = (dx2 >= 0.0)
-                     ? sqrt(dx2 + yterm[YT_DY2]) / (1.0 + sqrt(xterm[XT_XNORM2] + yterm[YT_YNORM2]))
-                     : -1.0;
+  out[ST_STEP] = (dx2 >= 0.0) ? step : -1.0;
   out[ST_NEG] = e1;
   out[ST_COMP] = e2;
   out[ST_SG] = sg;
@@ -614,10 +680,11 @@ __global__ void __launch_bounds__(XTraits<K>::T)
     samples[tid] = msk;
   }
   {
+    using PO = PartOps<TA>;
     const TA* Pp = static_cast<const TA*>(p.Ppart);
     TA acc[K];
 #pragma unroll
-    for (int a = 0; a < K; ++a) acc[a] = TA(0);
+    for (int a = 0; a < K; ++a) acc[a] = PO::zero();
     if (active)
       for (int q0 = warp; q0 < Q; q0 += NW * 4) {   // four partials in flight per thread
         TA w[4][K];
@@ -625,12 +692,12 @@ __global__ void __launch_bounds__(XTraits<K>::T)
         for (int u = 0; u < 4; ++u) {
           const int qq = q0 + u * NW;
 #pragma unroll
-          for (int a = 0; a < K; ++a) w[u][a] = qq < Q ? Pp[((size_t)qq * p.ld + row) * K + a] : TA(0);
+          for (int a = 0; a < K; ++a) w[u][a] = qq < Q ? Pp[((size_t)qq * p.ld + row) * K + a] : PO::zero();
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int a = 0; a < K; ++a) acc[a] += w[u][a];
+          for (int a = 0; a < K; ++a) acc[a] = PO::add(acc[a], w[u][a]);
       }
 #pragma unroll
     for (int a = 0; a < K; ++a) psum[warp][lane][a] = acc[a];
@@ -639,7 +706,7 @@ __global__ void __launch_bounds__(XTraits<K>::T)
   NnlsSolver<K> solver;
   solver.init(H, 2.220446049250313e-16);
   if (mode == MODE_SWEEP) {
-    if (TABLE) build_subset_table<K>(solver, tab, tok);
+    if constexpr (TABLE) build_subset_table_lanes<K>(solver, tab, tok, 0, T, [] { __syncthreads(); });
     else build_cache<K>(&cache, solver, samples, CACHE_N);
   }
 
@@ -661,8 +728,10 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       double pr = 0.0, xo = 0.0;
       uint32_t old_mask = 0;
       if (comp) {
+        TA ts = psum[0][lrow][g.a];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) pr += (double)psum[w][lrow][g.a];
+        for (int w = 1; w < NW; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][g.a]);
+        pr = PartOps<TA>::to_double(ts);
         xo = p.X[cur][(size_t)grow_i * K + g.a];
       }
       if (ract) old_mask = p.xmask[cur][grow_i];
@@ -745,12 +814,18 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       if (lane < 16) term_w[warp][lane] = (lane == XT_XMAX) ? mx : tr;
       if (mode == MODE_SWEEP) {
         if (comp) {
+          const float hi = __double2float_rn(xn);
           p.X[nxt][(size_t)grow_i * K + g.a] = xn;
-          p.X32[nxt][(size_t)grow_i * K + g.a] = (float)xn;
+          p.X32[nxt][(size_t)grow_i * K + g.a] = hi;
+          p.X32lo[nxt][(size_t)grow_i * K + g.a] = __double2float_rn(xn - (double)hi);
         }
         if (ract && g.a == 0) p.xmask[nxt][grow_i] = msk;
       } else {
-        if (comp) p.X32[cur][(size_t)grow_i * K + g.a] = (float)xo;
+        if (comp) {
+          const float hi = __double2float_rn(xo);
+          p.X32[cur][(size_t)grow_i * K + g.a] = hi;
+          p.X32lo[cur][(size_t)grow_i * K + g.a] = __double2float_rn(xo - (double)hi);
+        }
         if (ract && g.a == 0) p.xmask[cur][grow_i] = msk;
       }
     }
@@ -775,10 +850,10 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       double pr[K], xo[K], xn[K];
 #pragma unroll
       for (int a = 0; a < K; ++a) {
-        double t = 0.0;
+        TA ts = psum[0][lane][a];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) t += (double)psum[w][lane][a];
-        pr[a] = t;
+        for (int w = 1; w < NW; ++w) ts = PartOps<TA>::add(ts, psum[w][lane][a]);
+        pr[a] = PartOps<TA>::to_double(ts);
         xo[a] = p.X[cur][(size_t)row * K + a];
         xn[a] = xo[a];
       }
@@ -829,13 +904,19 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       if (mode == MODE_SWEEP) {
 #pragma unroll
         for (int a = 0; a < K; ++a) {
+          const float hi = __double2float_rn(xn[a]);
           p.X[nxt][(size_t)row * K + a] = xn[a];
-          p.X32[nxt][(size_t)row * K + a] = (float)xn[a];
+          p.X32[nxt][(size_t)row * K + a] = hi;
+          p.X32lo[nxt][(size_t)row * K + a] = __double2float_rn(xn[a] - (double)hi);
         }
         p.xmask[nxt][row] = msk;
       } else {
 #pragma unroll
-        for (int a = 0; a < K; ++a) p.X32[cur][(size_t)row * K + a] = (float)xo[a];
+        for (int a = 0; a < K; ++a) {
+          const float hi = __double2float_rn(xo[a]);
+          p.X32[cur][(size_t)row * K + a] = hi;
+          p.X32lo[cur][(size_t)row * K + a] = __double2float_rn(xo[a] - (double)hi);
+        }
         p.xmask[cur][row] = msk;
       }
     }
@@ -869,11 +950,16 @@ __global__ void __launch_bounds__(XTraits<K>::T)
     Gs[tid] = fin[tid];
   }
   __syncthreads();
-  if (TABLE) {   // subset table of the new G for the next M pass (global memory)
+  if constexpr (TABLE && K > 6) {   // subset table of the new G for the next M pass (k = 7, 8: global memory)
     NnlsSolver<K> gs;
     gs.init(Gs, 2.220446049250313e-16);
-    build_subset_table<K>(gs, p.Gtab, p.Gok);
+    build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 0, T, [] { __syncthreads(); });
   }
+  double rec[NSTAT];
+  if (warp == 0 && mode != MODE_PRIME)
+    // statistics of iterate t: Y half from this sweep's M pass, X half from
+    // the sweep that produced X_t
+    combine_stats_warp(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
   if (tid == 0) {
     double xt[NXT];
     for (int e = 0; e < NXT; ++e) xt[e] = fin[K * K + e];
@@ -881,10 +967,6 @@ __global__ void __launch_bounds__(XTraits<K>::T)
     if (mode == MODE_PRIME) {
       for (int e = 0; e < NXT; ++e) st->xiter[cur][e] = xt[e];
     } else {
-      // statistics of iterate t: Y half from this sweep's M pass, X half from
-      // the sweep that produced X_t
-      double rec[NSTAT];
-      combine_stats(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
       rec[ST_CHANGED_ROWS] = fin[K * K + XT_CHANGED];
       rec[ST_NOTCONV] += fin[K * K + XT_NOTCONV];
       for (int e = 0; e < NSTAT; ++e) st->stats[iter % STAT_CAP][e] = rec[e];
