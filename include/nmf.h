@@ -217,6 +217,84 @@ nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launch
 nmf_status nmf_sweep_noalloc(const float *M, int64_t n, int64_t m, int64_t ldm, int32_t k,
                              double *X, double *Y, double *stats_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent problems of uneven n, m and k, each the
+ * problem of Sec. 1 with its own stopping test, swept together.  The paper
+ * solves one problem at a time; batching is a deployment form of the same
+ * sweep (every problem's iterates are those nmf_sweep would produce for the
+ * same partition of its columns into groups).
+ *
+ * Execution: problems are grouped into classes by (k, cluster size); each
+ * class runs one persistent launch whose clusters claim work items in list
+ * order -- for every sweep, the M-pass items (problem, column group) of every
+ * problem, then its row-pass items (problem, group of row blocks) -- with
+ * per-problem dependency counters and bounded waits.  The classes run
+ * concurrently on forked streams, and one replay of 16 sweeps is captured in
+ * a CUDA graph.  The mixed-precision schedule runs on the device per problem:
+ * FP32 passes until the relative KKT error reaches mixed_switch or has not
+ * improved by 2% over 256 sweeps, then compensated (double-float) passes; a
+ * problem stops at its own kkt_target / stol and drops out of later items.
+ * Results do not depend on which other problems share the batch.
+ * ------------------------------------------------------------------------ */
+typedef struct nmf_batch nmf_batch;
+
+/* Create a batch of nprob problems, problem j configured by cfgs[j] (prec
+ * must be NMF_PREC_MIXED; the cuda_stream fields are ignored: every problem's
+ * work is ordered on the batch's stream, cuda_stream here, NULL: the library
+ * creates one).  Allocates each problem's device memory as nmf_create does.
+ * Returns NMF_EINVAL for nprob < 1 or an unsupported configuration. */
+nmf_status nmf_batch_create(const nmf_config *cfgs, int32_t nprob, void *cuda_stream, nmf_batch **out);
+
+/* Release the batch and every problem in it (synchronises its stream). */
+nmf_status nmf_batch_destroy(nmf_batch *b);
+
+/* Number of problems; the handle of problem j (owned by the batch: use it
+ * for read-only calls such as nmf_objective_kkt, never nmf_destroy). */
+int32_t nmf_batch_size(const nmf_batch *b);
+nmf_handle *nmf_batch_problem(nmf_batch *b, int32_t j);
+
+/* Per-problem data, with the arguments and errors of nmf_append_columns,
+ * nmf_set_factors and nmf_get_factors for problem j (0 <= j < nprob). */
+nmf_status nmf_batch_append_columns(nmf_batch *b, int32_t j, const void *cols, int64_t ncols, int64_t ld,
+                                    int32_t dtype, int32_t on_device);
+nmf_status nmf_batch_set_factors(nmf_batch *b, int32_t j, const double *X, const double *Y,
+                                 int32_t on_device);
+nmf_status nmf_batch_get_factors(nmf_batch *b, int32_t j, double *X, double *Y, uint32_t *xmask,
+                                 uint32_t *ymask, int32_t on_device);
+
+/* Pass mode of every problem: -1 the device schedule above (default), 0 FP32
+ * passes only, 2 compensated passes only.  Fixed modes stop on the targets
+ * at every sweep.  Other values: NMF_EINVAL. */
+nmf_status nmf_batch_set_pass_mode(nmf_batch *b, int32_t mode);
+
+/* Schedule of the persistent launches: columns per M-pass item (the column
+ * groups of each problem, so also the number of partials its row pass
+ * reduces) and the largest number of TMA stages of the M pass (1..8).  The
+ * partition of a problem's columns depends on cols_per_item, so results
+ * agree across schedules to rounding only. */
+nmf_status nmf_batch_set_schedule(nmf_batch *b, int32_t cols_per_item, int32_t stage_cap);
+
+/* Sweep every problem that has factors and columns: max_sweeps > 0 sweeps at
+ * most (fewer when every problem stops), 0: until every problem stops,
+ * capped by the largest max_sweeps of the configurations (NMF_ENOTCONV when
+ * the cap is reached first).  stats: NULL or nprob records, record j as
+ * nmf_sweep would fill it for problem j (fp64_sweeps counts compensated
+ * sweeps).  sweeps_run: NULL or the number of batch sweeps launched.
+ * Synchronises the batch's stream after every 16 sweeps. */
+nmf_status nmf_batch_sweep(nmf_batch *b, int32_t max_sweeps, nmf_stats *stats, int32_t *sweeps_run);
+
+/* Autotuner: times every candidate schedule (cols_per_item in {16, 32, 64,
+ * 128, 256} x stage_cap in {2, 8}) over trial_sweeps FP32-pass sweeps of the
+ * batch as it stands and keeps the fastest; the tuning sweeps are ordinary
+ * sweeps of the iteration (the problems advance).  Outputs (NULL allowed):
+ * the chosen schedule and its time per batch sweep in ms. */
+nmf_status nmf_batch_autotune(nmf_batch *b, int32_t trial_sweeps, int32_t *cols_per_item, int32_t *stage_cap,
+                              double *best_ms_per_sweep);
+
+/* Kernel launches issued by the batch (graph replays count their launches). */
+int64_t nmf_batch_launch_count(const nmf_batch *b);
+const char *nmf_batch_last_error(const nmf_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ from . import _native
 from ._native import (NMF_DTYPE_F32, NMF_DTYPE_F64, NMF_PREC_FP64, NMF_PREC_MIXED, NMF_WARM_COLD,
                       NMF_WARM_PREV, NMFError, check, load, nmf_config, nmf_stats)
 
-__all__ = ["StreamingNMF", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
+__all__ = ["StreamingNMF", "StreamingNMFBatch", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
            "NMF_PREC_MIXED", "NMF_DTYPE_F32", "NMF_DTYPE_F64", "NMF_WARM_COLD", "NMF_WARM_PREV"]
 
 
@@ -27,6 +27,32 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return a.data_ptr(), int(a.is_cuda)
     raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _cols_arg(cols):
+    """(address, ncols, ld, dtype, on_device, keep-alive) of n x c columns."""
+    if isinstance(cols, np.ndarray):
+        a = np.asfortranarray(cols)
+        dtype = NMF_DTYPE_F32 if a.dtype == np.float32 else NMF_DTYPE_F64
+        if a.dtype not in (np.float32, np.float64):
+            a = np.asfortranarray(a, dtype=np.float64)
+            dtype = NMF_DTYPE_F64
+        return a.ctypes.data, int(a.shape[1]), int(max(a.shape[0], 1)), dtype, 0, a
+    t = cols   # torch tensor, column-major view expected: stride (1, ld)
+    if t.stride(0) != 1:
+        t = t.t().contiguous().t()
+    dtype = NMF_DTYPE_F32 if str(t.dtype) == "torch.float32" else NMF_DTYPE_F64
+    return t.data_ptr(), int(t.shape[1]), int(max(t.stride(1), 1)), dtype, int(t.is_cuda), t
+
+
+def _config(lib, n, k, m_capacity, prec, kkt_target, stol, mixed_switch, max_sweeps, warm_start, stream):
+    cfg = nmf_config()
+    lib.nmf_config_init(C.byref(cfg))
+    cfg.n, cfg.m_capacity, cfg.k, cfg.prec = int(n), int(m_capacity), int(k), int(prec)
+    cfg.kkt_target, cfg.stol, cfg.mixed_switch = float(kkt_target), float(stol), float(mixed_switch)
+    cfg.max_sweeps, cfg.warm_start = int(max_sweeps), int(warm_start)
+    cfg.cuda_stream = stream
+    return cfg
 
 
 class StreamingNMF:
@@ -49,22 +75,8 @@ class StreamingNMF:
     # -- data -------------------------------------------------------------------
     def append_columns(self, cols):
         """cols: n x c (numpy or torch, float32/float64); any strides with unit row stride."""
-        if isinstance(cols, np.ndarray):
-            a = np.asfortranarray(cols)
-            dtype = NMF_DTYPE_F32 if a.dtype == np.float32 else NMF_DTYPE_F64
-            if a.dtype not in (np.float32, np.float64):
-                a = np.asfortranarray(a, dtype=np.float64)
-                dtype = NMF_DTYPE_F64
-            ptr, dev, ncols, ld = a.ctypes.data, 0, a.shape[1], a.shape[0]
-            keep = a
-        else:   # torch tensor, column-major view expected: stride (1, ld)
-            t = cols
-            if t.stride(0) != 1:
-                t = t.t().contiguous().t()
-            dtype = NMF_DTYPE_F32 if str(t.dtype) == "torch.float32" else NMF_DTYPE_F64
-            ptr, dev, ncols, ld = t.data_ptr(), int(t.is_cuda), t.shape[1], t.stride(1)
-            keep = t
-        st = self.lib.nmf_append_columns(self.h, C.c_void_p(ptr), int(ncols), int(max(ld, 1)), dtype, dev)
+        ptr, ncols, ld, dtype, dev, keep = _cols_arg(cols)
+        st = self.lib.nmf_append_columns(self.h, C.c_void_p(ptr), ncols, ld, dtype, dev)
         del keep
         return check(st, self.h)
 
@@ -123,6 +135,103 @@ class StreamingNMF:
         if getattr(self, "h", None):
             self.lib.nmf_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class StreamingNMFBatch:
+    """Many independent problems (n_j, k_j, m_capacity_j) swept together by the
+    batched persistent launches of the library (FP32 M, mixed precision)."""
+
+    def __init__(self, shapes, kkt_target=1e-8, stol=0.0, mixed_switch=1e-6, max_sweeps=100000,
+                 warm_start=NMF_WARM_PREV, stream=None):
+        self.lib = load()
+        self.shapes = [(int(n), int(k), int(mc)) for n, k, mc in shapes]
+        arr = (nmf_config * len(self.shapes))()
+        for j, (n, k, mc) in enumerate(self.shapes):
+            arr[j] = _config(self.lib, n, k, mc, NMF_PREC_MIXED, kkt_target, stol, mixed_switch, max_sweeps,
+                             warm_start, None)
+        b = C.c_void_p()
+        check(self.lib.nmf_batch_create(arr, len(self.shapes), stream, C.byref(b)))
+        self.b = b
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def _chk(self, st):
+        return check(st, batch=self.b)
+
+    def append_columns(self, j, cols):
+        ptr, ncols, ld, dtype, dev, keep = _cols_arg(cols)
+        st = self.lib.nmf_batch_append_columns(self.b, int(j), C.c_void_p(ptr), ncols, ld, dtype, dev)
+        del keep
+        return self._chk(st)
+
+    def m(self, j):
+        return int(self.lib.nmf_num_columns(self.lib.nmf_batch_problem(self.b, int(j))))
+
+    def set_factors(self, j, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.asfortranarray(Y, dtype=np.float64)
+        self._chk(self.lib.nmf_batch_set_factors(self.b, int(j), C.c_void_p(X.ctypes.data),
+                                                 C.c_void_p(Y.ctypes.data), 0))
+
+    def get_factors(self, j):
+        n, k, _ = self.shapes[j]
+        m = self.m(j)
+        X = np.zeros((n, k))
+        Y = np.zeros((k, m), order="F")
+        xm = np.zeros(n, dtype=np.uint32)
+        ym = np.zeros(m, dtype=np.uint32)
+        self._chk(self.lib.nmf_batch_get_factors(self.b, int(j), C.c_void_p(X.ctypes.data),
+                                                 C.c_void_p(Y.ctypes.data), C.c_void_p(xm.ctypes.data),
+                                                 C.c_void_p(ym.ctypes.data), 0))
+        return X, np.ascontiguousarray(Y), xm, ym
+
+    def set_pass_mode(self, mode):
+        self._chk(self.lib.nmf_batch_set_pass_mode(self.b, int(mode)))
+
+    def set_schedule(self, cols_per_item, stage_cap=8):
+        self._chk(self.lib.nmf_batch_set_schedule(self.b, int(cols_per_item), int(stage_cap)))
+
+    def sweep(self, max_sweeps=0, allow_notconv=False):
+        """Returns (per-problem statistics, batch sweeps launched)."""
+        sts = (nmf_stats * len(self.shapes))()
+        nrun = C.c_int32()
+        s = self.lib.nmf_batch_sweep(self.b, int(max_sweeps), sts, C.byref(nrun))
+        if not (allow_notconv and s == _native.NMF_ENOTCONV):
+            self._chk(s)
+        return [sts[j].as_dict() for j in range(len(self.shapes))], int(nrun.value)
+
+    def autotune(self, trial_sweeps=3):
+        c, sc, ms = C.c_int32(), C.c_int32(), C.c_double()
+        self._chk(self.lib.nmf_batch_autotune(self.b, int(trial_sweeps), C.byref(c), C.byref(sc), C.byref(ms)))
+        return {"cols_per_item": c.value, "stage_cap": sc.value, "ms_per_sweep": ms.value}
+
+    def objective_kkt(self, j):
+        h = self.lib.nmf_batch_problem(self.b, int(j))
+        f, e, r = C.c_double(), C.c_double(), C.c_double()
+        check(self.lib.nmf_objective_kkt(h, C.byref(f), C.byref(e), C.byref(r)), h)
+        return {"f": f.value, "kkt_abs": e.value, "kkt_rel": r.value}
+
+    @property
+    def launches(self):
+        return int(self.lib.nmf_batch_launch_count(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.nmf_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -22,7 +22,16 @@ NMF_WARM_COLD, NMF_WARM_PREV = 0, 1
 EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns", "nmf_num_columns",
            "nmf_set_factors", "nmf_get_factors", "nmf_sweep", "nmf_set_pass_mode",
            "nmf_objective_kkt", "nmf_status_string", "nmf_last_error", "nmf_launch_count",
-           "nmf_set_timing", "nmf_get_timing", "nmf_sweep_noalloc")
+           "nmf_set_timing", "nmf_get_timing", "nmf_sweep_noalloc",
+           "nmf_batch_create", "nmf_batch_destroy", "nmf_batch_size", "nmf_batch_problem",
+           "nmf_batch_append_columns", "nmf_batch_set_factors", "nmf_batch_get_factors",
+           "nmf_batch_set_pass_mode", "nmf_batch_set_schedule", "nmf_batch_sweep", "nmf_batch_autotune",
+           "nmf_batch_launch_count", "nmf_batch_last_error")
+
+# exports whose return value is not an nmf_status
+_NON_STATUS = ("nmf_config_init", "nmf_num_columns", "nmf_status_string", "nmf_last_error",
+               "nmf_launch_count", "nmf_batch_size", "nmf_batch_problem", "nmf_batch_launch_count",
+               "nmf_batch_last_error")
 
 
 class nmf_config(C.Structure):
@@ -85,18 +94,42 @@ def load(path: str = LIB_PATH):
                                  C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.nmf_sweep_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    B = C.c_void_p
+    L.nmf_batch_create.argtypes = [C.POINTER(nmf_config), C.c_int32, C.c_void_p, C.POINTER(B)]
+    L.nmf_batch_destroy.argtypes = [B]
+    L.nmf_batch_size.argtypes = [B]
+    L.nmf_batch_size.restype = C.c_int32
+    L.nmf_batch_problem.argtypes = [B, C.c_int32]
+    L.nmf_batch_problem.restype = H
+    L.nmf_batch_append_columns.argtypes = [B, C.c_int32, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                           C.c_int32]
+    L.nmf_batch_set_factors.argtypes = [B, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]
+    L.nmf_batch_get_factors.argtypes = [B, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int32]
+    L.nmf_batch_set_pass_mode.argtypes = [B, C.c_int32]
+    L.nmf_batch_set_schedule.argtypes = [B, C.c_int32, C.c_int32]
+    L.nmf_batch_sweep.argtypes = [B, C.c_int32, C.POINTER(nmf_stats), C.POINTER(C.c_int32)]
+    L.nmf_batch_autotune.argtypes = [B, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]
+    L.nmf_batch_launch_count.argtypes = [B]
+    L.nmf_batch_launch_count.restype = C.c_int64
+    L.nmf_batch_last_error.argtypes = [B]
+    L.nmf_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("nmf_config_init", "nmf_num_columns", "nmf_status_string", "nmf_last_error",
-                        "nmf_launch_count"):
+        if name not in _NON_STATUS:
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
 
 
-def check(status: int, handle=None):
+def check(status: int, handle=None, batch=None):
     if status != NMF_OK:
         L = load()
-        detail = L.nmf_last_error(handle).decode() if handle else ""
+        detail = ""
+        if handle:
+            detail = L.nmf_last_error(handle).decode()
+        elif batch:
+            detail = L.nmf_batch_last_error(batch).decode()
         raise NMFError(status, "%s%s" % (L.nmf_status_string(status).decode(),
                                          (": " + detail) if detail else ""))
     return status

@@ -7,7 +7,7 @@
 #include <string>
 
 #include "../../include/nmf.h"
-#include "nmf_launch.cuh"
+#include "nmf_internal.h"
 
 using namespace nmfgb;
 
@@ -770,3 +770,60 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// internal interface for the batched form
+// ---------------------------------------------------------------------------
+namespace nmfgb {
+
+bool handle_info(nmf_handle* h, HandleInfo* o) {
+  if (!h || !o) return false;
+  o->n = h->n;
+  o->ld = h->ld;
+  o->k = h->k;
+  o->m = h->m;
+  o->mcap = h->mcap;
+  o->nsm = h->nsm;
+  o->smem_optin = h->smem_optin;
+  o->nxblk = h->nxblk;
+  o->store_f32 = h->store_f32;
+  o->factors_set = h->factors_set;
+  o->qcap = h->nsm;
+  o->phase = h->phase;
+  o->dSt = h->dSt;
+  o->hSt = h->hSt;
+  o->stream = h->stream;
+  return true;
+}
+
+bool handle_problem(nmf_handle* h, int var, Problem* out) {
+  if (!h || var < 0 || var >= NVAR || !h->has[var]) return false;
+  *out = make_problem(h, var);
+  return true;
+}
+
+bool handle_plan(nmf_handle* h, int var, YPlan* out) {
+  if (!h || var < 0 || var >= NVAR || !h->has[var]) return false;
+  return make_plan(h, var, out);
+}
+
+const KernelSet* handle_kernels(nmf_handle* h, int var) {
+  if (!h || var < 0 || var >= NVAR || !h->has[var]) return nullptr;
+  return &h->ks[var];
+}
+
+nmf_status handle_sync_state(nmf_handle* h) { return read_state(h); }
+
+void handle_set_phase(nmf_handle* h, int phase) {
+  h->phase = phase;
+  h->snap_valid = false;
+}
+
+void handle_fill_stats(nmf_handle* h, int measured, int sweeps, int fp64_sweeps, nmf_stats* out) {
+  fill_stats(h, measured, sweeps, fp64_sweeps, out);
+}
+
+nmf_status handle_fail(nmf_handle* h, nmf_status s, const char* msg) { return fail(h, s, msg); }
+
+}  // namespace nmfgb
+

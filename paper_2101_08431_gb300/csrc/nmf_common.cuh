@@ -44,10 +44,22 @@ struct DevState {
   unsigned err;      // ERR_* bits
   unsigned xblocks_done;   // last-block counter of the X kernel
   int stop_reason;   // 1 = rel-KKT target, 2 = step tolerance
-  int pad[3];
+  int pass_var;      // device-driven mixed schedule: variant of the next sweep's passes
+  int since_best;    // sweeps since the best FP32-pass relative KKT improved by 2%
+  int fp64_sweeps;   // sweeps whose tail ran with an FP64-class M pass (counts up)
   double stats[STAT_CAP][NSTAT];
   double xiter[2][NXT];     // X-half terms of the iterate held in buffers 0 / 1
   double msq;               // ||M||_F^2 of the resident window
+  double best_rel;          // device-driven mixed schedule: best FP32-pass relative KKT (< 0: none)
+};
+
+// Arithmetic of one M pass.
+enum Variant {
+  VAR_F32 = 0,   // FP32 M, FP32 contraction (mixed precision, bulk sweeps)
+  VAR_REF = 1,   // FP32 M, FP64 contraction (mixed precision, refinement sweeps)
+  VAR_F64 = 2,   // FP64 M, FP64 contraction (the plain FP64 form)
+  VAR_DF = 3,    // FP32 M, compensated FP32 contraction (mixed precision, refinement sweeps)
+  NVAR = 4
 };
 
 // One problem as the kernels see it.
@@ -76,6 +88,12 @@ struct Problem {
   double stol;            // <= 0 disables
   int warm;               // 0 cold, 1 previous sweep (new columns are seeded at append)
   int fp64_pass;          // 1 when this sweep's M pass runs in FP64
+  // device-driven mixed schedule (batched form): FP32 passes until the
+  // relative KKT reaches mixed_switch or has not improved by 2% for
+  // stall_sweeps sweeps, then compensated passes (DevState::pass_var)
+  int auto_mixed;
+  int stall_sweeps;
+  double mixed_switch;
 };
 
 enum Mode { MODE_SWEEP = 0, MODE_PRIME = 1, MODE_KKT = 2 };
@@ -90,6 +108,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
+}
+
+// Release store / acquire load of a 32-bit flag at GPU scope.
+__device__ __forceinline__ void st_release_u32(unsigned* a, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init() {

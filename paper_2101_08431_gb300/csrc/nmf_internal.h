@@ -1,0 +1,31 @@
+// Internal interface between the one-problem handle (nmf_api.cu) and the
+// batched form (nmf_batch.cu).  Not part of the C ABI.
+#pragma once
+
+#include "../../include/nmf.h"
+#include "nmf_launch.cuh"
+
+namespace nmfgb {
+
+struct HandleInfo {
+  int n, ld, k, m, mcap, nsm, smem_optin, nxblk;
+  bool store_f32, factors_set;
+  int qcap;             // capacity of the partial buffers (column groups)
+  int phase;            // host mixed schedule: 0 FP32 passes, 1 refinement passes
+  DevState* dSt;        // device control block
+  const DevState* hSt;  // its host mirror (valid after handle_sync_state)
+  cudaStream_t stream;
+};
+
+bool handle_info(nmf_handle* h, HandleInfo* out);
+// the problem as variant `var` sees it (kkt_target / stol of that variant)
+bool handle_problem(nmf_handle* h, int var, Problem* out);
+// the one-problem launch plan of variant `var` (cluster size and rows per CTA)
+bool handle_plan(nmf_handle* h, int var, YPlan* out);
+const KernelSet* handle_kernels(nmf_handle* h, int var);
+nmf_status handle_sync_state(nmf_handle* h);
+void handle_set_phase(nmf_handle* h, int phase);
+void handle_fill_stats(nmf_handle* h, int measured, int sweeps, int fp64_sweeps, nmf_stats* out);
+nmf_status handle_fail(nmf_handle* h, nmf_status s, const char* msg);
+
+}  // namespace nmfgb

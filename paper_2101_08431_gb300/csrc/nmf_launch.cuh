@@ -5,15 +5,6 @@
 
 namespace nmfgb {
 
-// Arithmetic of one M pass.
-enum Variant {
-  VAR_F32 = 0,   // FP32 M, FP32 contraction (mixed precision, bulk sweeps)
-  VAR_REF = 1,   // FP32 M, FP64 contraction (mixed precision, refinement sweeps)
-  VAR_F64 = 2,   // FP64 M, FP64 contraction (the plain FP64 form)
-  VAR_DF = 3,    // FP32 M, compensated FP32 contraction (mixed precision, refinement sweeps)
-  NVAR = 4
-};
-
 struct YPlan {
   int C, R, Q, S;
   size_t smem;
@@ -94,7 +85,7 @@ int max_clusters_y(int C, size_t smem) {
 template <typename TA, int K>
 cudaError_t launch_x(const Problem& p, int mode, int Q, int nxblk, cudaStream_t s) {
   auto kern = xpass_kernel<TA, K>;
-  constexpr size_t dyn = XSmem<K>::bytes();
+  constexpr size_t dyn = XSmem<TA, K>::bytes();
   static bool attr_done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -103,7 +94,7 @@ cudaError_t launch_x(const Problem& p, int mode, int Q, int nxblk, cudaStream_t 
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
-  kern<<<nxblk, XTraits<K>::T, dyn, s>>>(p, mode, Q, nxblk, nullptr);
+  kern<<<nxblk, XTraits<K>::T, dyn, s>>>(p, mode, Q, nxblk);
   return cudaGetLastError();
 }
 

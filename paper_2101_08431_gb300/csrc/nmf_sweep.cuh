@@ -77,22 +77,25 @@ struct YSmem {
   __host__ __device__ static size_t stage_bytes(int R) { return size_t(Tr::TJ) * R * sizeof(TM); }
 };
 
+// The M pass of column group q (of Q) by one cluster of C CTAs, each owning
+// R rows; smem_raw: the dynamic shared memory (small part, S stages, and the
+// P accumulators when the policy keeps them there).  Called by all threads
+// of the CTA; leaves every barrier it used invalidated, so that a persistent
+// caller can run it again on the same memory.
 template <typename TM, typename AR, int K>
-__global__ void __launch_bounds__(512, 1)
-    ypass_kernel(Problem p, int mode, int S, int C, int R, int Q) {
+__device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, int C, int R, int Q, int q,
+                                           unsigned char* smem_raw) {
   using Tr = YTraits<TM, AR, K>;
   using Sm = YSmem<TM, AR, K>;
   using VT = typename AR::V;
   using AT = typename AR::A;
   constexpr int TC = Tr::TC, NCW = Tr::NCW, RPT = Tr::RPT, TJ = Tr::TJ, VP = Tr::VP;
   constexpr bool TABLE = K <= 8;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   typename Sm::Small& sm = *reinterpret_cast<typename Sm::Small*>(smem_raw);
   TM* stages = reinterpret_cast<TM*>(smem_raw + Sm::small_bytes());
 
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
-  const int q = blockIdx.x / C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   DevState* st = p.st;
   if (st->done) return;                       // uniform: written by an earlier launch
@@ -534,7 +537,23 @@ __global__ void __launch_bounds__(512, 1)
     }
   }
   if (timed_out) set_err(st, ERR_TIMEOUT);
+  __syncthreads();
+  if (tid == 0) {
+    for (int s2 = 0; s2 < S; ++s2) mbar_inval(&sm.full[s2]);
+    for (int b = 0; b < 2; ++b) {
+      mbar_inval(&sm.bready[b]);
+      mbar_inval(&sm.yready[b]);
+      mbar_inval(&sm.xbar[b]);
+    }
+  }
   if (C > 1) cluster.sync();
+}
+
+template <typename TM, typename AR, int K>
+__global__ void __launch_bounds__(512, 1)
+    ypass_kernel(Problem p, int mode, int S, int C, int R, int Q) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  ypass_body<TM, AR, K>(p, mode, S, C, R, Q, (int)blockIdx.x / C, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -588,7 +607,7 @@ __device__ inline void combine_stats_warp(const double* yterm, const double* xte
 
 template <int K>
 struct XTraits {
-  static constexpr int NW = K >= 16 ? 4 : 8;   // warps (static smem bound at k = 16)
+  static constexpr int NW = 16;          // warps
   static constexpr int T = NW * 32;
   static constexpr int RB = 32;          // rows per block (lane <-> row)
   static constexpr int NV = K * K + NXT; // Gram partial + X-half terms
@@ -628,45 +647,67 @@ __device__ void tree_sum(const double* src, int nparts, size_t stride, int nval,
   }
 }
 
-// Dynamic shared memory of the row pass: the subset table of H (k <= 8).
-template <int K>
+// Dynamic shared memory of the row pass: the working arrays, then the
+// subset table of H (k <= 8).
+template <typename TA, int K>
 struct XSmem {
+  using Tr = XTraits<K>;
   static constexpr bool TABLE = K <= 8;
+  static constexpr int NWN = TABLE ? Tr::RB / LaneGroup<K>::CPW : 1;   // NNLS warps (k <= 8)
+  struct Small {
+    double H[K * K];
+    double Gs[K * K];
+    TA psum[Tr::NW][Tr::RB][K];
+    double fin[Tr::NV];
+    double yfin[NYT];
+    uint32_t samples[CACHE_N];
+    InvCache<K> cache;
+    double gram_w[NWN][K * K];
+    double term_w[NWN][16];
+    unsigned ticket;
+  };
+  static constexpr size_t SMALL = (sizeof(Small) + 127) & ~size_t(127);
   static constexpr size_t TAB = TABLE ? (size_t(1) << K) * K * K * sizeof(double) : 0;
   static constexpr size_t OK = TABLE ? (size_t(1) << K) * sizeof(int) : 0;
-  static constexpr size_t bytes() { return TAB + OK + 16; }
+  __host__ __device__ static constexpr size_t bytes() { return SMALL + TAB + OK + 16; }
 };
 
-// Row pass: rows [32 b, 32 b + 32) of X.  The 8 warps split the cluster
-// partials of P = M Y^T (lane <-> row, accumulated in the pass's precision)
-// and build the subset table of H; warp 0 solves the 32 row NNLS problems
-// and forms the X-half terms and the Gram partial; the last block to finish
-// combines the blocks, forms G = X^T X and its subset table for the next
-// M pass, and the statistics of the iterate.
+// Row pass: rows [32 b, 32 b + 32) of X.  The 16 warps split the cluster
+// partials of P = M Y^T (lane <-> row, summed in the partials' own type) and
+// build the subset table of H; k <= 8: 32 / CPW warps solve the 32 row NNLS
+// problems lane-parallel (lane <-> (row, component)) and form the X-half
+// terms and the Gram partial (k = 16: warp 0, one row per lane); the last
+// block to finish combines the blocks, forms G = X^T X (and its subset table
+// for k = 7, 8), and the statistics of the iterate.
+//
+// blk: the row block; xsm_raw: XSmem<TA, K>::bytes() of shared memory.
+// tail_done (may be null): the block that runs the last-block tail stores
+// tail_value there (release) once the tail's results are visible.
 template <typename TA, int K>
-__global__ void __launch_bounds__(XTraits<K>::T)
-    xpass_kernel(Problem p, int mode, int Q, int nxblk, double* kkt_out) {
+__device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, int nxblk, int blk,
+                                           unsigned char* xsm_raw, unsigned* tail_done,
+                                           unsigned tail_value) {
   using Tr = XTraits<K>;
-  using Xs = XSmem<K>;
+  using Xs = XSmem<TA, K>;
   constexpr int T = Tr::T, NW = Tr::NW, RB = Tr::RB, NV = Tr::NV;
   constexpr bool TABLE = Xs::TABLE;
-  extern __shared__ __align__(16) unsigned char xsm_raw[];
-  double* tab = reinterpret_cast<double*>(xsm_raw);
-  int* tok = reinterpret_cast<int*>(xsm_raw + Xs::TAB);
-  __shared__ double H[K * K];
-  __shared__ double Gs[K * K];
-  __shared__ TA psum[NW][RB][K];
-  __shared__ double fin[NV];
-  __shared__ double yfin[NYT];
-  __shared__ uint32_t samples[CACHE_N];
-  __shared__ InvCache<K> cache;
-  __shared__ unsigned ticket;
+  typename Xs::Small& xs = *reinterpret_cast<typename Xs::Small*>(xsm_raw);
+  double* tab = reinterpret_cast<double*>(xsm_raw + Xs::SMALL);
+  int* tok = reinterpret_cast<int*>(xsm_raw + Xs::SMALL + Xs::TAB);
+  double* H = xs.H;
+  double* Gs = xs.Gs;
+  auto& psum = xs.psum;
+  double* fin = xs.fin;
+  double* yfin = xs.yfin;
+  uint32_t* samples = xs.samples;
+  InvCache<K>& cache = xs.cache;
+  unsigned& ticket = xs.ticket;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   DevState* st = p.st;
   if (st->done) return;
   const int iter = st->iter;
   const int cur = iter & 1, nxt = cur ^ 1;
-  const int row0 = blockIdx.x * RB;
+  const int row0 = blk * RB;
   const int row = row0 + lane;
   const bool active = row < p.n;
 
@@ -713,8 +754,8 @@ __global__ void __launch_bounds__(XTraits<K>::T)
   if (TABLE) {
     // lanes <-> (row slot jj, component a): warps 0 .. NWN-1 hold the 32 rows
     constexpr int KP = LaneGroup<K>::KP, CPW = LaneGroup<K>::CPW, NWN = RB / CPW;
-    __shared__ double gram_w[NWN][K * K];
-    __shared__ double term_w[NWN][16];
+    auto& gram_w = xs.gram_w;
+    auto& term_w = xs.term_w;
     if (warp < NWN) {
       LaneGroup<K> g;
       g.init();
@@ -839,7 +880,7 @@ __global__ void __launch_bounds__(XTraits<K>::T)
         const int te = e - K * K;
         for (int w = 0; w < NWN; ++w) r = (te == XT_XMAX) ? dmax_nn(r, term_w[w][te]) : r + term_w[w][te];
       }
-      p.Xpart[(size_t)blockIdx.x * NV + e] = r;
+      p.Xpart[(size_t)blk * NV + e] = r;
     }
     __threadfence();
   } else if (warp == 0) {
@@ -931,7 +972,7 @@ __global__ void __launch_bounds__(XTraits<K>::T)
         for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
         const double r = warp_reduce_scatter<32, double>(chunk);
         const int e = c * 32 + lane;
-        if (e < NV) p.Xpart[(size_t)blockIdx.x * NV + e] = (e == K * K + XT_XMAX) ? mx : r;
+        if (e < NV) p.Xpart[(size_t)blk * NV + e] = (e == K * K + XT_XMAX) ? mx : r;
       }
     }
     __threadfence();
@@ -971,6 +1012,17 @@ __global__ void __launch_bounds__(XTraits<K>::T)
       rec[ST_NOTCONV] += fin[K * K + XT_NOTCONV];
       for (int e = 0; e < NSTAT; ++e) st->stats[iter % STAT_CAP][e] = rec[e];
       for (int e = 0; e < NXT; ++e) st->xiter[nxt][e] = xt[e];
+      if (p.fp64_pass) ++st->fp64_sweeps;
+      if (p.auto_mixed && st->pass_var != VAR_DF && rec[ST_VALID] > 0.0) {
+        const double rel = rec[ST_REL];
+        if (st->best_rel < 0.0 || rel < 0.98 * st->best_rel) {
+          st->best_rel = rel;
+          st->since_best = 0;
+        } else {
+          ++st->since_best;
+        }
+        if (rel <= p.mixed_switch || st->since_best >= p.stall_sweeps) st->pass_var = VAR_DF;
+      }
       const bool kkt_ok = p.kkt_target > 0.0 && rec[ST_VALID] > 0.0 && rec[ST_REL] <= p.kkt_target;
       const bool step_ok = p.stol > 0.0 && rec[ST_STEP] >= 0.0 && rec[ST_STEP] <= p.stol;
       if (kkt_ok) {
@@ -987,6 +1039,20 @@ __global__ void __launch_bounds__(XTraits<K>::T)
     st->xblocks_done = 0;
     __threadfence();
   }
+  if (tail_done) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release_u32(tail_done, tail_value);
+    }
+  }
+}
+
+template <typename TA, int K>
+__global__ void __launch_bounds__(XTraits<K>::T)
+    xpass_kernel(Problem p, int mode, int Q, int nxblk) {
+  extern __shared__ __align__(128) unsigned char xsm_raw[];
+  xpass_body<TA, K>(p, mode, Q, nxblk, (int)blockIdx.x, xsm_raw, nullptr, 0u);
 }
 
 }  // namespace nmfgb

@@ -53,6 +53,27 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.nmf_destroy(None) == _native.NMF_OK
 
 
+def test_batch_arguments_rejected_before_any_device_work(lib):
+    from paper_2101_08431_gb300 import _native
+    cfgs = (_native.nmf_config * 2)()
+    for j in range(2):
+        lib.nmf_config_init(C.byref(cfgs[j]))
+        cfgs[j].n, cfgs[j].k, cfgs[j].m_capacity = 100, 4, 10
+    b = C.c_void_p()
+    assert lib.nmf_batch_create(None, 2, None, C.byref(b)) == _native.NMF_EINVAL
+    assert lib.nmf_batch_create(cfgs, 0, None, C.byref(b)) == _native.NMF_EINVAL
+    cfgs[1].prec = _native.NMF_PREC_FP64          # the batched form is mixed precision
+    assert lib.nmf_batch_create(cfgs, 2, None, C.byref(b)) == _native.NMF_EINVAL
+    cfgs[1].prec, cfgs[1].k = _native.NMF_PREC_MIXED, 9
+    assert lib.nmf_batch_create(cfgs, 2, None, C.byref(b)) == _native.NMF_EINVAL
+    assert lib.nmf_batch_size(None) == 0
+    assert lib.nmf_batch_problem(None, 0) is None
+    assert lib.nmf_batch_set_pass_mode(None, 0) == _native.NMF_EINVAL
+    assert lib.nmf_batch_set_schedule(None, 64, 8) == _native.NMF_EINVAL
+    assert lib.nmf_batch_sweep(None, 1, None, None) == _native.NMF_EINVAL
+    assert lib.nmf_batch_destroy(None) == _native.NMF_OK
+
+
 def test_library_is_built_for_sm_103a_only():
     from paper_2101_08431_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
