@@ -6,7 +6,7 @@
 #include <cstring>
 #include <string>
 
-#include "../../include/nmf.h"
+#include "nmf.h"
 #include "nmf_internal.h"
 
 using namespace nmfgb;
@@ -148,6 +148,9 @@ struct nmf_handle {
   double* dG = nullptr;
   double* dGtab = nullptr;
   int* dGok = nullptr;
+  double* dHg = nullptr;
+  double* dHtab = nullptr;
+  int* dHok = nullptr;
   double* dColsq = nullptr;
   void* dPpart = nullptr;
   double* dHpart = nullptr;
@@ -259,6 +262,9 @@ Problem make_problem(const nmf_handle* h, int var) {
   p.G = h->dG;
   p.Gtab = h->dGtab;
   p.Gok = h->dGok;
+  p.Hg = h->dHg;
+  p.Htab = h->dHtab;
+  p.Hok = h->dHok;
   p.colsq = h->dColsq;
   p.Ppart = h->dPpart;
   p.Hpart = h->dHpart;
@@ -402,7 +408,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
     for (int j = 0; j < 3; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
   void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dX32lo[0], h->dX32lo[1], h->dY[0], h->dY[1],
-                   h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dColsq, h->dPpart,
+                   h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dHg, h->dHtab, h->dHok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage};
   for (void* p : dptrs)
@@ -484,6 +490,9 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   if (k <= 8) {
     ok &= dalloc(&h->dGtab, ((size_t)1 << k) * k * k) == cudaSuccess;
     ok &= dalloc(&h->dGok, (size_t)1 << k) == cudaSuccess;
+    ok &= dalloc(&h->dHg, (size_t)k * k) == cudaSuccess;
+    ok &= dalloc(&h->dHtab, ((size_t)1 << k) * k * k) == cudaSuccess;
+    ok &= dalloc(&h->dHok, (size_t)1 << k) == cudaSuccess;
   }
   ok &= dalloc(&h->dColsq, h->mcap) == cudaSuccess;
   ok &= cudaMalloc(&h->dPpart, (size_t)Qmax * h->ld * k * 8) == cudaSuccess;

@@ -6,6 +6,8 @@
 // device control block); the batch adds the work lists, the dependency
 // counters, the device-driven mixed schedule and the autotuner.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -20,7 +22,7 @@ namespace {
 
 constexpr int BATCH_CHUNK = 16;                  // sweeps per graph replay
 constexpr int STALL_SWEEPS = 256;                // FP32 sweeps without 2% progress before switching
-constexpr unsigned SMEM_RESERVE = 128;           // claim words behind the bodies' budget
+constexpr unsigned SMEM_RESERVE = 128;           // claim words and a flag behind the bodies' budget
 
 // stop flags, schedule state and sweep counters of every problem at the
 // start of a batched call; pass_init: the variant each problem resumes with
@@ -168,6 +170,7 @@ nmf_status build_plan(nmf_batch* b) {
     if (!handle_problem(b->h[j], VAR_F32, &bp.pv[0]) || !handle_problem(b->h[j], VAR_DF, &bp.pv[1]))
       return bfail(b, NMF_EINVAL, "no problem view");
     for (int v = 0; v < 2; ++v) {
+      bp.pv[v].tab_global = 1;
       bp.pv[v].auto_mixed = b->force_var < 0 ? 1 : 0;
       bp.pv[v].stall_sweeps = STALL_SWEEPS;
       bp.pv[v].mixed_switch = b->cfg[j].mixed_switch;
@@ -196,7 +199,12 @@ nmf_status build_plan(nmf_batch* b) {
     Class& c = b->cls[it->second];
     c.probs.push_back(j);
     hp[it->second].push_back(bp);
-    const double w = (double)hi.n * hi.m * hi.k;
+    // CTA time of one sweep (cycles, rough): the M-pass items are paced by
+    // their tiles (the NNLS warp's solve and the rows' contraction), the
+    // row-pass items by their row blocks
+    const int cpc = (hi.m + Q - 1) / Q;
+    const double tiles = (double)((cpc + k0->TJ - 1) / k0->TJ);
+    const double w = (double)Q * C * tiles * (4000.0 + (double)R * k0->TJ * hi.k / 16.0) + hi.nxblk * 4000.0;
     c.work += w;
     total_work += w;
   }
@@ -217,7 +225,8 @@ nmf_status build_plan(nmf_batch* b) {
     BCUDA(b, cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming));
     const int fit = std::max(1, batch_max_clusters(c.k, c.C));
     const int items = off[n] + off[2 * n + 1];
-    int g = (int)((double)fit * c.work / std::max(total_work, 1.0) + 0.5);
+    // CTAs in proportion to the class's share of the work
+    int g = (int)((double)b->nsm * c.work / std::max(total_work, 1.0) / c.C + 0.5);
     c.nclusters = std::max(1, std::min(g, std::min(fit, items)));
     BatchArgs& a = c.args;
     a.probs = c.dProbs;
@@ -236,14 +245,42 @@ nmf_status build_plan(nmf_batch* b) {
 
 // Enqueue `nsweeps` sweeps of every class on the batch stream (fork / join).
 nmf_status enqueue_sweeps(nmf_batch* b, int nsweeps) {
+  // NMF_DEBUG_BATCH: the class table and each class kernel's time (outside
+  // graph capture only)
+  static const bool dbg = std::getenv("NMF_DEBUG_BATCH") != nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(b->stream, &cs);
+  const bool timed = dbg && cs == cudaStreamCaptureStatusNone;
+  std::vector<cudaEvent_t> evs;
   BCUDA(b, cudaEventRecord(b->fork, b->stream));
   for (Class& c : b->cls) {
     BCUDA(b, cudaStreamWaitEvent(c.s, b->fork, 0));
     BCUDA(b, cudaMemsetAsync(c.dCnt, 0, sizeof(unsigned) * (1 + 2 * c.probs.size()), c.s));
     c.args.nsweeps = nsweeps;
+    if (timed) {
+      evs.emplace_back();
+      cudaEventCreate(&evs.back());
+      cudaEventRecord(evs.back(), c.s);
+    }
     BCUDA(b, launch_batch(c.k, c.args, c.C, c.nclusters, c.s));
+    if (timed) {
+      evs.emplace_back();
+      cudaEventCreate(&evs.back());
+      cudaEventRecord(evs.back(), c.s);
+    }
     BCUDA(b, cudaEventRecord(c.ev, c.s));
     BCUDA(b, cudaStreamWaitEvent(b->stream, c.ev, 0));
+  }
+  if (timed) {
+    cudaStreamSynchronize(b->stream);
+    for (size_t i = 0; i < b->cls.size(); ++i) {
+      const Class& c = b->cls[i];
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]);
+      std::fprintf(stderr, "nmf batch class k=%d C=%d problems=%zu clusters=%d sweeps=%d: %.3f ms\n", c.k, c.C,
+                   c.probs.size(), c.nclusters, nsweeps, ms);
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
   }
   batch_count_kernel<<<1, 256, 0, b->stream>>>(b->dSts, (int)b->h.size(), b->dDone);
   BCUDA(b, cudaGetLastError());

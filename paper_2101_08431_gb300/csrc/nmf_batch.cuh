@@ -8,8 +8,9 @@
 // and run the same bodies as the one-problem kernels.  Per-problem
 // dependencies are global counters: an M-pass item of sweep s waits until
 // the problem's tail of sweep s-1 has published its results (t_done >= s);
-// a row-pass item waits until every M-pass CTA of its sweep has finished
-// (a_done >= (s+1) Q C).  Items are claimed in list order and depend only on
+// a row-pass item waits until every M-pass CTA of its sweep has finished and
+// (k <= 8) the H stage run by the last of them has published H and its
+// subset table (a_done >= (s+1) (Q C + 1)).  Items are claimed in list order and depend only on
 // items earlier in the list, which are held by running clusters, so every
 // wait ends; each wait is bounded all the same (ERR_TIMEOUT, and the
 // problem is stopped so that nothing waits on it).  A problem whose tail
@@ -70,10 +71,26 @@ __device__ __forceinline__ void batch_wait(const unsigned* ctr, unsigned target,
   __threadfence();
 }
 
+// H stage of problem p after its M pass (k <= 8): H = Y Y^T from the Q
+// cluster partials (the same fixed-order tree as the row pass), and its
+// subset table, into the problem's global buffers; every row block of the
+// sweep then reads them instead of forming them itself.  All 512 threads.
+template <int K>
+__device__ void batch_h_stage(const Problem& p, int Q, unsigned char* smem_raw) {
+  double* H = reinterpret_cast<double*>(smem_raw);
+  tree_sum<512>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += 512) p.Hg[e] = H[e];
+  NnlsSolver<K> solver;
+  solver.init(H, 2.220446049250313e-16);
+  build_subset_table_lanes<K>(solver, p.Htab, p.Hok, 0, 512, [] { __syncthreads(); });
+}
+
 template <int K>
 __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned* s_item = reinterpret_cast<unsigned*>(smem_raw + a.smem_budget);   // two claim words
+  unsigned* s_item = reinterpret_cast<unsigned*>(smem_raw + a.smem_budget);   // two claim words, a flag
+  constexpr unsigned HS = K <= 8 ? 1u : 0u;   // H-stage increments of a_done per sweep
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int crank = (int)cluster.block_rank();
@@ -107,9 +124,23 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs a) {
         else
           ypass_body<float, ArDF, K>(bp.pv[1], MODE_SWEEP, bp.S[1], C, bp.R, bp.Q, q, smem_raw);
         __syncthreads();
+        // the CTA that completes the sweep's M pass of the problem runs its H stage
+        const unsigned per = (unsigned)(bp.Q * C) + HS;
         if (threadIdx.x == 0) {
           __threadfence();
-          atomicAdd(&a.a_done[j], 1u);
+          const unsigned old = atomicAdd(&a.a_done[j], 1u);
+          s_item[2] = (HS && old + 1u == (unsigned)(s + 1) * per - HS) ? 1u : 0u;
+        }
+        __syncthreads();
+        if constexpr (HS != 0) {
+          if (s_item[2]) {
+            batch_h_stage<K>(bp.pv[0], bp.Q, smem_raw);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+              __threadfence();
+              atomicAdd(&a.a_done[j], 1u);
+            }
+          }
         }
       }
     } else {
@@ -119,7 +150,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs a) {
       const BatchProb& bp = a.probs[j];
       DevState* st = bp.pv[0].st;
       const int blk = (r - a.boff[j]) * C + crank;
-      if (threadIdx.x == 0) batch_wait(&a.a_done[j], (unsigned)((s + 1) * bp.Q * C), st);
+      if (threadIdx.x == 0) batch_wait(&a.a_done[j], (unsigned)(s + 1) * ((unsigned)(bp.Q * C) + HS), st);
       __syncthreads();
       if (blk < bp.nxblk && !*reinterpret_cast<volatile int*>(&st->done)) {
         // the variant of this sweep (the tail that may change it runs after

@@ -47,6 +47,7 @@ struct DevState {
   int pass_var;      // device-driven mixed schedule: variant of the next sweep's passes
   int since_best;    // sweeps since the best FP32-pass relative KKT improved by 2%
   int fp64_sweeps;   // sweeps whose tail ran with an FP64-class M pass (counts up)
+  int gtab_valid;    // the subset table of G in global memory belongs to the current G
   double stats[STAT_CAP][NSTAT];
   double xiter[2][NXT];     // X-half terms of the iterate held in buffers 0 / 1
   double msq;               // ||M||_F^2 of the resident window
@@ -78,6 +79,11 @@ struct Problem {
   double* G;              // k x k, X^T X of the current iterate
   double* Gtab;           // k <= 8: inv(G_PP) for every passive set P (2^k x k x k)
   int* Gok;               // k <= 8: 1 where the table entry is valid
+  double* Hg;             // k <= 8, tab_global: H = Y Y^T of this sweep (k x k)
+  double* Htab;           // k <= 8, tab_global: its subset table (2^k x k x k)
+  int* Hok;
+  int tab_global;         // 1: the tables of G and H are built once per sweep into global
+                          // memory (G by the row pass's tail, H by the batch's H stage)
   const double* colsq;    // ||M_{:,j}||^2 per physical column
   void* Ppart;            // [Q][ld][k] partial M Y^T (accumulate type)
   double* Hpart;          // [Q][k][k]

@@ -2,7 +2,7 @@
 // batched form (nmf_batch.cu).  Not part of the C ABI.
 #pragma once
 
-#include "../../include/nmf.h"
+#include "nmf.h"
 #include "nmf_launch.cuh"
 
 namespace nmfgb {

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/nmf.h"
+#include "nmf.h"
 #include "nmf_launch.cuh"
 
 using namespace nmfgb;

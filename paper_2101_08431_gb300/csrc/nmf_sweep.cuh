@@ -331,8 +331,11 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
       double hacc[K];   // row a of H = Y Y^T over this warp's column slots
 #pragma unroll
       for (int c = 0; c < K; ++c) hacc[c] = 0.0;
-      const double* gtab = K <= 6 ? sm.gtab : p.Gtab;
-      const int* gok = K <= 6 ? sm.gok : p.Gok;
+      // k = 7, 8 always, k <= 6 when the row pass's tail has built it: the
+      // table of G in global memory; otherwise this warp builds it below
+      const bool gglob = K > 6 || (p.tab_global && st->gtab_valid);
+      const double* gtab = gglob ? p.Gtab : sm.gtab;
+      const int* gok = gglob ? p.Gok : sm.gok;
       // warm start and passive set of the next tile, fetched one tile ahead
       double yo_nx = 0.0;
       uint32_t om_nx = 0;
@@ -343,7 +346,7 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         om_nx = p.ymask[cur][ph_nx];
       }
       if constexpr (K <= 6) {
-        if (mode == MODE_SWEEP)
+        if (mode == MODE_SWEEP && !gglob)
           build_subset_table_lanes<K>(solver, sm.gtab, sm.gok, NCW * 32, 32, [] { __syncwarp(); });
       }
       for (int t = 0; t < ntiles; ++t) {
@@ -692,8 +695,10 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   constexpr int T = Tr::T, NW = Tr::NW, RB = Tr::RB, NV = Tr::NV;
   constexpr bool TABLE = Xs::TABLE;
   typename Xs::Small& xs = *reinterpret_cast<typename Xs::Small*>(xsm_raw);
-  double* tab = reinterpret_cast<double*>(xsm_raw + Xs::SMALL);
-  int* tok = reinterpret_cast<int*>(xsm_raw + Xs::SMALL + Xs::TAB);
+  // tab_global: H and its subset table come from the batch's H stage
+  const bool hglob = TABLE && p.tab_global && mode == MODE_SWEEP;
+  double* tab = hglob ? p.Htab : reinterpret_cast<double*>(xsm_raw + Xs::SMALL);
+  int* tok = hglob ? p.Hok : reinterpret_cast<int*>(xsm_raw + Xs::SMALL + Xs::TAB);
   double* H = xs.H;
   double* Gs = xs.Gs;
   auto& psum = xs.psum;
@@ -711,7 +716,11 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   const int row = row0 + lane;
   const bool active = row < p.n;
 
-  tree_sum<T>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
+  if (hglob) {
+    for (int e = tid; e < K * K; e += T) H[e] = p.Hg[e];
+  } else {
+    tree_sum<T>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
+  }
   if (!TABLE && tid < CACHE_N) {
     uint32_t msk = 0;
     if (mode == MODE_SWEEP && p.warm) {
@@ -747,8 +756,11 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   NnlsSolver<K> solver;
   solver.init(H, 2.220446049250313e-16);
   if (mode == MODE_SWEEP) {
-    if constexpr (TABLE) build_subset_table_lanes<K>(solver, tab, tok, 0, T, [] { __syncthreads(); });
-    else build_cache<K>(&cache, solver, samples, CACHE_N);
+    if constexpr (TABLE) {
+      if (!hglob) build_subset_table_lanes<K>(solver, tab, tok, 0, T, [] { __syncthreads(); });
+    } else {
+      build_cache<K>(&cache, solver, samples, CACHE_N);
+    }
   }
 
   if (TABLE) {
@@ -991,10 +1003,15 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     Gs[tid] = fin[tid];
   }
   __syncthreads();
-  if constexpr (TABLE && K > 6) {   // subset table of the new G for the next M pass (k = 7, 8: global memory)
-    NnlsSolver<K> gs;
-    gs.init(Gs, 2.220446049250313e-16);
-    build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 0, T, [] { __syncthreads(); });
+  // subset table of the new G for the next M pass in global memory: always
+  // for k = 7, 8; for k <= 6 when tab_global (otherwise the M pass builds it)
+  const bool gbuilt = TABLE && (K > 6 || p.tab_global);
+  if constexpr (TABLE) {
+    if (gbuilt) {
+      NnlsSolver<K> gs;
+      gs.init(Gs, 2.220446049250313e-16);
+      build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 0, T, [] { __syncthreads(); });
+    }
   }
   double rec[NSTAT];
   if (warp == 0 && mode != MODE_PRIME)
@@ -1002,6 +1019,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     // the sweep that produced X_t
     combine_stats_warp(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
   if (tid == 0) {
+    st->gtab_valid = gbuilt ? 1 : 0;
     double xt[NXT];
     for (int e = 0; e < NXT; ++e) xt[e] = fin[K * K + e];
     xt[XT_VALID] = 1.0;
