@@ -319,6 +319,9 @@ def run_ours(args):
     # ---- batched persistent form: 256 uneven problems
     if not args.skip_batch:
         out["batched"] = batched_leg(args, rank, sptr, barrier, max_over_ranks, world)
+    # ---- streaming serving: 32 streams, Poisson chunk arrivals
+    if not args.skip_serve:
+        out["serving"] = serving_leg(args, rank, sptr)
     # ---- CPU baseline (rank 0 at N = 1 only)
     if rank == 0 and world == 1 and not args.skip_cpu:
         v, nsw, dt = cpu_sweep_rate(M64, X0, Y0)
@@ -338,7 +341,7 @@ def run_ours(args):
                        "state": "steady state: timed sweeps follow %d sweeps from the U[0,1] start" % PRECOND,
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU"}}
     for key in ("roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks", "refine_pass", "fp64_form",
-                "time_to_kkt", "batched"):
+                "time_to_kkt", "batched", "serving"):
         if key in out:
             line[key] = out[key]
     print(json.dumps(line), flush=True)
@@ -410,6 +413,87 @@ def batched_leg(args, rank, sptr, barrier, max_over_ranks, world):
     return res
 
 
+SERVE_STREAMS, SERVE_N, SERVE_K, SERVE_CAP = 32, 2048, 6, 8192
+SERVE_RATE, SERVE_INIT = 200.0, 256
+
+
+def serving_leg(args, rank, sptr):
+    """Streaming serving: 32 streams (n=2048, k=6, history capped at 8192
+    resident columns), FP32 M.  Each stream first receives SERVE_INIT columns
+    (solved to the target, untimed); then chunks of U{1..64} columns arrive
+    with Poisson arrivals at 200 chunks/s in aggregate, each to a uniformly
+    drawn stream, for serve_seconds.  Reports per-chunk latency (arrival to
+    completion at relative KKT <= 1e-6), columns/s and the server's rounds."""
+    import synth
+    from paper_2101_08431_gb300 import StreamingServer
+    g = np.random.default_rng(7 + rank)
+    D = args.serve_seconds
+    horizon = SERVE_INIT + int(SERVE_RATE * D * 33.0 / SERVE_STREAMS * 2.0) + 256
+    data = []
+    for sidx in range(SERVE_STREAMS):
+        M, _, _ = synth.pdf_like(SERVE_N, horizon, SERVE_K, noise=NOISE, relative=True, seed=2000 + sidx)
+        data.append(np.asfortranarray(M, dtype=np.float32))
+    srv = StreamingServer(kkt_target=1e-6, max_sweeps_per_chunk=2000, sweeps_per_round=8, stream=sptr)
+    ids = [srv.open_stream(SERVE_N, SERVE_K, SERVE_CAP, seed=2000 + i) for i in range(SERVE_STREAMS)]
+    pos = [0] * SERVE_STREAMS
+    t_init = time.perf_counter()
+    pend = set()
+    for i, sid in enumerate(ids):
+        pend.add(srv.submit(sid, data[i][:, :SERVE_INIT]))
+        pos[i] = SERVE_INIT
+    while pend:
+        for r in srv.poll(wait_ms=100):
+            pend.discard(r["ticket"])
+    init_s = time.perf_counter() - t_init
+    st0 = srv.stats()
+    # the timed phase: Poisson arrivals
+    arrivals, t = [], 0.0
+    while True:
+        t += g.exponential(1.0 / SERVE_RATE)
+        if t >= D:
+            break
+        arrivals.append((t, int(g.integers(0, SERVE_STREAMS)), int(g.integers(1, 65))))
+    lat, cols_done, pend = [], 0, set()
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(arrivals) or pend:
+        now = time.perf_counter() - t0
+        while k < len(arrivals) and arrivals[k][0] <= now:
+            _, i, c = arrivals[k]
+            if pos[i] + c > horizon:
+                c = max(0, horizon - pos[i])
+            if c:
+                pend.add(srv.submit(ids[i], data[i][:, pos[i]:pos[i] + c]))
+                pos[i] += c
+            k += 1
+        wait = 0 if k < len(arrivals) else 50
+        nxt = arrivals[k][0] - (time.perf_counter() - t0) if k < len(arrivals) else 0.0
+        for r in srv.poll(wait_ms=max(0, min(int(nxt * 1e3), 2)) if k < len(arrivals) else wait):
+            if r["ticket"] in pend:
+                pend.discard(r["ticket"])
+                lat.append(r["t_done_s"] - r["t_submit_s"])
+                cols_done += r["ncols"]
+        if k < len(arrivals):
+            time.sleep(max(0.0, min(0.001, arrivals[k][0] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    rounds = st["rounds"] - st0["rounds"]
+    return {"workload": "%d streams, n=%d, k=%d, history cap %d columns, FP32 M; chunks U{1..64} columns, "
+                        "Poisson arrivals %.0f chunks/s for %.0f s" % (SERVE_STREAMS, SERVE_N, SERVE_K, SERVE_CAP,
+                                                                      SERVE_RATE, D),
+            "target": "relative KKT <= 1e-6 per chunk (2000 sweeps at most)",
+            "chunks": int(len(lat)), "columns": int(cols_done), "columns_per_s": cols_done / wall,
+            "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "latency_p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+            "latency_mean_ms": float(lat.mean() * 1e3) if len(lat) else None,
+            "rounds": rounds, "batch_sweeps": st["batch_sweeps"] - st0["batch_sweeps"],
+            "streams_per_round": (st["stream_rounds"] - st0["stream_rounds"]) / max(rounds, 1),
+            "streams_admitted": st["streams_admitted"], "hbm_in_use_gb": st["hbm_in_use_bytes"] / 1e9,
+            "init_s": init_s}
+
+
 def run_ncu_case(args):
     """A short, fixed launch sequence for ncu captures: priming, PRECOND_NCU
     sweeps of the chosen pass, then 3 more (capture them with -s/-c)."""
@@ -439,6 +523,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-ttk", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-problem batched leg")
+    ap.add_argument("--skip-serve", action="store_true", help="skip the streaming-serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--batch-ttk", action="store_true",
                     help="also run every batched problem to relative KKT 1e-8")
     ap.add_argument("--ncu-case", choices=["f32", "ref", "f64"], default=None,

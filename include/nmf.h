@@ -295,6 +295,98 @@ nmf_status nmf_batch_autotune(nmf_batch *b, int32_t trial_sweeps, int32_t *cols_
 int64_t nmf_batch_launch_count(const nmf_batch *b);
 const char *nmf_batch_last_error(const nmf_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Streaming server: many streams whose time columns arrive in chunks (the
+ * streaming setting of Sec. 1), served by a worker thread of the library.
+ * Every admitted stream's ring of columns (capacity m_capacity; older
+ * columns are evicted), X, Y and passive sets stay resident on the device;
+ * each chunk is appended with its columns warm-started from the stream's
+ * last column (y and passive set) and the stream's current X.  Rounds:
+ * append every chunk that has arrived, then run sweeps_per_round batched
+ * sweeps (the batched form above) over every stream with chunks in flight
+ * -- continuous batching: chunks that arrive during a round join at the
+ * next round, and the work of all streams of a round overlaps in the same
+ * launches.  A chunk completes, together with the stream's other chunks in
+ * flight, when the stream's relative KKT error reaches kkt_target, or after
+ * max_sweeps_per_chunk sweeps.  Streams are admitted in the order they were
+ * opened while their device footprint fits hbm_budget_bytes and at most
+ * max_streams are resident; closing a stream (after its chunks complete)
+ * frees its memory for the next one.  A stream's results do not depend on
+ * the other streams being served (the batched form's property), for the
+ * same sequence of its own chunks and rounds.
+ * ------------------------------------------------------------------------ */
+typedef struct nmf_server nmf_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;     /* device bytes the streams may hold; 0: 90% of free memory */
+    int32_t max_streams;          /* resident streams at most                              */
+    int32_t max_sweeps_per_chunk; /* a chunk completes after this many sweeps at most      */
+    int32_t sweeps_per_round;     /* batched sweeps per round                              */
+    int32_t pad;
+    double kkt_target;            /* relative KKT target of a chunk                        */
+    double mixed_switch;          /* the mixed schedule's switch (as nmf_config)           */
+    void *cuda_stream;            /* stream of the server's device work, or NULL           */
+} nmf_server_config;
+
+typedef struct {
+    uint64_t ticket;              /* from nmf_server_submit                                */
+    int32_t stream;
+    int32_t ncols;                /* columns of the chunk                                  */
+    double t_submit_s, t_done_s;  /* seconds since the server was created                  */
+    int32_t sweeps;               /* sweeps the stream ran between the chunk's round and completion */
+    int32_t converged;            /* 1: kkt_target met; 0: max_sweeps_per_chunk reached    */
+    double kkt_rel, f;            /* of the stream's last measured iterate                 */
+    int32_t m;                    /* resident columns of the stream at completion          */
+    int32_t pad;
+} nmf_chunk_result;
+
+typedef struct {
+    int64_t chunks_done, columns_done, rounds, batch_sweeps;
+    int64_t stream_rounds;        /* sum over rounds of the streams swept in the round     */
+    int32_t max_streams_in_round;
+    int32_t streams_admitted, streams_queued, pad;
+    int64_t hbm_in_use_bytes, hbm_budget_bytes;
+} nmf_server_stats;
+
+/* Defaults: hbm_budget 0 (90% of free memory), max_streams 64,
+ * max_sweeps_per_chunk 500, sweeps_per_round 8, kkt_target 1e-6,
+ * mixed_switch 1e-6. */
+void nmf_server_config_init(nmf_server_config *cfg);
+
+/* Start a server (and its worker thread) on the current device. */
+nmf_status nmf_server_create(const nmf_server_config *cfg, nmf_server **out);
+
+/* Stop the worker (chunks still in flight are dropped) and free everything. */
+nmf_status nmf_server_destroy(nmf_server *s);
+
+/* Open a stream of n rows, rank k (1..8 or 16) and m_capacity resident
+ * columns; seed draws its U[0,1] starting factors.  The stream is queued for
+ * admission (chunks may be submitted at once; they wait).  NMF_ECAPACITY if
+ * its footprint alone exceeds the budget. */
+nmf_status nmf_server_open_stream(nmf_server *s, int64_t n, int32_t k, int64_t m_capacity, uint64_t seed,
+                                  int32_t *id);
+
+/* Submit a chunk: ncols >= 1 FP32 host columns, column-major with leading
+ * dimension ld >= n (copied before return).  *ticket (may be NULL)
+ * identifies its result. */
+nmf_status nmf_server_submit(nmf_server *s, int32_t id, const float *cols, int64_t ncols, int64_t ld,
+                             uint64_t *ticket);
+
+/* Close a stream once its chunks have completed (no more submissions). */
+nmf_status nmf_server_close_stream(nmf_server *s, int32_t id);
+
+/* Completed chunks, oldest first: up to cap results into out, their number
+ * in *nout; waits up to wait_ms for the first one when none is ready. */
+nmf_status nmf_server_poll(nmf_server *s, nmf_chunk_result *out, int32_t cap, int32_t *nout, int32_t wait_ms);
+
+/* The stream's current factors (host buffers: X n x k, Y k x m with m the
+ * resident columns, returned in *m; masks may be NULL), between rounds. */
+nmf_status nmf_server_get_factors(nmf_server *s, int32_t id, double *X, double *Y, uint32_t *xmask,
+                                  uint32_t *ymask, int64_t *m);
+
+nmf_status nmf_server_get_stats(nmf_server *s, nmf_server_stats *out);
+const char *nmf_server_last_error(nmf_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ from . import _native
 from ._native import (NMF_DTYPE_F32, NMF_DTYPE_F64, NMF_PREC_FP64, NMF_PREC_MIXED, NMF_WARM_COLD,
                       NMF_WARM_PREV, NMFError, check, load, nmf_config, nmf_stats)
 
-__all__ = ["StreamingNMF", "StreamingNMFBatch", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
+__all__ = ["StreamingNMF", "StreamingNMFBatch", "StreamingServer", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
            "NMF_PREC_MIXED", "NMF_DTYPE_F32", "NMF_DTYPE_F64", "NMF_WARM_COLD", "NMF_WARM_PREV"]
 
 
@@ -232,6 +232,89 @@ class StreamingNMFBatch:
         if getattr(self, "b", None):
             self.lib.nmf_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class StreamingServer:
+    """The library's streaming server: streams of time columns arriving in
+    chunks, served by a worker thread with continuous batching."""
+
+    def __init__(self, hbm_budget_bytes=0, max_streams=64, kkt_target=1e-6, mixed_switch=1e-6,
+                 max_sweeps_per_chunk=500, sweeps_per_round=8, stream=None):
+        self.lib = load()
+        cfg = _native.nmf_server_config()
+        self.lib.nmf_server_config_init(C.byref(cfg))
+        cfg.hbm_budget_bytes, cfg.max_streams = int(hbm_budget_bytes), int(max_streams)
+        cfg.kkt_target, cfg.mixed_switch = float(kkt_target), float(mixed_switch)
+        cfg.max_sweeps_per_chunk, cfg.sweeps_per_round = int(max_sweeps_per_chunk), int(sweeps_per_round)
+        cfg.cuda_stream = stream
+        s = C.c_void_p()
+        check(self.lib.nmf_server_create(C.byref(cfg), C.byref(s)))
+        self.s = s
+        self.shape = {}
+
+    def _chk(self, st):
+        if st != _native.NMF_OK:
+            detail = self.lib.nmf_server_last_error(self.s).decode() if self.s else ""
+            raise NMFError(st, "%s%s" % (self.lib.nmf_status_string(st).decode(), (": " + detail) if detail else ""))
+        return st
+
+    def open_stream(self, n, k, m_capacity, seed=0):
+        i = C.c_int32()
+        self._chk(self.lib.nmf_server_open_stream(self.s, int(n), int(k), int(m_capacity), int(seed), C.byref(i)))
+        self.shape[i.value] = (int(n), int(k), int(m_capacity))
+        return i.value
+
+    def submit(self, sid, cols):
+        """cols: n x c float32 (numpy); returns the chunk's ticket."""
+        a = np.asfortranarray(cols, dtype=np.float32)
+        t = C.c_uint64()
+        self._chk(self.lib.nmf_server_submit(self.s, int(sid), C.c_void_p(a.ctypes.data), int(a.shape[1]),
+                                             int(a.shape[0]), C.byref(t)))
+        return int(t.value)
+
+    def close_stream(self, sid):
+        self._chk(self.lib.nmf_server_close_stream(self.s, int(sid)))
+
+    def poll(self, wait_ms=0, cap=1024):
+        out = (_native.nmf_chunk_result * cap)()
+        n = C.c_int32()
+        self._chk(self.lib.nmf_server_poll(self.s, out, int(cap), C.byref(n), int(wait_ms)))
+        return [out[i].as_dict() for i in range(n.value)]
+
+    def get_factors(self, sid):
+        n, k, mcap = self.shape[sid]
+        X = np.zeros((n, k))
+        Y = np.zeros((k, mcap), order="F")
+        xm = np.zeros(n, dtype=np.uint32)
+        ym = np.zeros(mcap, dtype=np.uint32)
+        m = C.c_int64()
+        self._chk(self.lib.nmf_server_get_factors(self.s, int(sid), C.c_void_p(X.ctypes.data),
+                                                  C.c_void_p(Y.ctypes.data), C.c_void_p(xm.ctypes.data),
+                                                  C.c_void_p(ym.ctypes.data), C.byref(m)))
+        mm = int(m.value)
+        return X, np.ascontiguousarray(Y[:, :mm]), xm, ym[:mm]
+
+    def stats(self):
+        st = _native.nmf_server_stats()
+        self._chk(self.lib.nmf_server_get_stats(self.s, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.nmf_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

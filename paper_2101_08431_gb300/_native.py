@@ -26,12 +26,15 @@ EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns",
            "nmf_batch_create", "nmf_batch_destroy", "nmf_batch_size", "nmf_batch_problem",
            "nmf_batch_append_columns", "nmf_batch_set_factors", "nmf_batch_get_factors",
            "nmf_batch_set_pass_mode", "nmf_batch_set_schedule", "nmf_batch_sweep", "nmf_batch_autotune",
-           "nmf_batch_launch_count", "nmf_batch_last_error")
+           "nmf_batch_launch_count", "nmf_batch_last_error",
+           "nmf_server_config_init", "nmf_server_create", "nmf_server_destroy", "nmf_server_open_stream",
+           "nmf_server_submit", "nmf_server_close_stream", "nmf_server_poll", "nmf_server_get_factors",
+           "nmf_server_get_stats", "nmf_server_last_error")
 
 # exports whose return value is not an nmf_status
 _NON_STATUS = ("nmf_config_init", "nmf_num_columns", "nmf_status_string", "nmf_last_error",
                "nmf_launch_count", "nmf_batch_size", "nmf_batch_problem", "nmf_batch_launch_count",
-               "nmf_batch_last_error")
+               "nmf_batch_last_error", "nmf_server_config_init", "nmf_server_last_error")
 
 
 class nmf_config(C.Structure):
@@ -46,6 +49,31 @@ class nmf_stats(C.Structure):
                 ("kkt_rel", C.c_double), ("step_rel", C.c_double), ("changed_cols", C.c_int64),
                 ("changed_rows", C.c_int64), ("nnls_notconv", C.c_int64), ("measured_iter", C.c_int32),
                 ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+class nmf_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_streams", C.c_int32), ("max_sweeps_per_chunk", C.c_int32),
+                ("sweeps_per_round", C.c_int32), ("pad", C.c_int32), ("kkt_target", C.c_double),
+                ("mixed_switch", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+class nmf_chunk_result(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("stream", C.c_int32), ("ncols", C.c_int32), ("t_submit_s", C.c_double),
+                ("t_done_s", C.c_double), ("sweeps", C.c_int32), ("converged", C.c_int32),
+                ("kkt_rel", C.c_double), ("f", C.c_double), ("m", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+class nmf_server_stats(C.Structure):
+    _fields_ = [("chunks_done", C.c_int64), ("columns_done", C.c_int64), ("rounds", C.c_int64),
+                ("batch_sweeps", C.c_int64), ("stream_rounds", C.c_int64), ("max_streams_in_round", C.c_int32),
+                ("streams_admitted", C.c_int32), ("streams_queued", C.c_int32), ("pad", C.c_int32),
+                ("hbm_in_use_bytes", C.c_int64), ("hbm_budget_bytes", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
@@ -115,6 +143,20 @@ def load(path: str = LIB_PATH):
     L.nmf_batch_launch_count.restype = C.c_int64
     L.nmf_batch_last_error.argtypes = [B]
     L.nmf_batch_last_error.restype = C.c_char_p
+    S = C.c_void_p
+    L.nmf_server_config_init.argtypes = [C.POINTER(nmf_server_config)]
+    L.nmf_server_config_init.restype = None
+    L.nmf_server_create.argtypes = [C.POINTER(nmf_server_config), C.POINTER(S)]
+    L.nmf_server_destroy.argtypes = [S]
+    L.nmf_server_open_stream.argtypes = [S, C.c_int64, C.c_int32, C.c_int64, C.c_uint64, C.POINTER(C.c_int32)]
+    L.nmf_server_submit.argtypes = [S, C.c_int32, C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_uint64)]
+    L.nmf_server_close_stream.argtypes = [S, C.c_int32]
+    L.nmf_server_poll.argtypes = [S, C.POINTER(nmf_chunk_result), C.c_int32, C.POINTER(C.c_int32), C.c_int32]
+    L.nmf_server_get_factors.argtypes = [S, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_int64)]
+    L.nmf_server_get_stats.argtypes = [S, C.POINTER(nmf_server_stats)]
+    L.nmf_server_last_error.argtypes = [S]
+    L.nmf_server_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in _NON_STATUS:
             getattr(L, name).restype = C.c_int

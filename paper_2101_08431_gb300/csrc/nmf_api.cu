@@ -785,6 +785,19 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
 // ---------------------------------------------------------------------------
 namespace nmfgb {
 
+int64_t handle_footprint(int64_t n, int k, int64_t mcap, bool store_f32, int nsm) {
+  const int64_t ld = (n + 31) / 32 * 32, nk = n * k, mk = mcap * k;
+  const int64_t nxblk = (n + XTraits<1>::RB - 1) / XTraits<1>::RB;
+  int64_t b = ld * mcap * (store_f32 ? 4 : 8);                       // the ring of M
+  b += 2 * (nk * 8 + 2 * nk * 4 + mk * 8 + mcap * 4 + n * 4);        // X, X32, X32lo, Y, masks
+  if (k <= 8) b += 2 * ((int64_t(1) << k) * k * k * 8 + (int64_t(1) << k) * 4 + k * k * 8);
+  b += mcap * 8;                                                     // column norms
+  b += (int64_t)nsm * (ld * k * 8 + k * k * 8 + NYT * 8);            // cluster partials
+  b += nxblk * (k * k + NXT) * 8 + (int64_t)sizeof(DevState) + 4096;
+  b += (int64_t)APPEND_STAGE_COLS * ld * 8;                          // append staging
+  return b;
+}
+
 bool handle_info(nmf_handle* h, HandleInfo* o) {
   if (!h || !o) return false;
   o->n = h->n;

@@ -24,16 +24,15 @@ constexpr int BATCH_CHUNK = 16;                  // sweeps per graph replay
 constexpr int STALL_SWEEPS = 256;                // FP32 sweeps without 2% progress before switching
 constexpr unsigned SMEM_RESERVE = 128;           // claim words and a flag behind the bodies' budget
 
-// stop flags, schedule state and sweep counters of every problem at the
-// start of a batched call; pass_init: the variant each problem resumes with
+// stop flags of every problem at the start of a batched call, and the
+// variant each problem resumes with (the schedule's progress record,
+// best_rel and since_best, carries over from call to call)
 __global__ void batch_reset_kernel(DevState* const* sts, const int* pass_init, int n) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     DevState* st = sts[j];
     st->done = 0;
     st->stop_reason = 0;
     st->pass_var = pass_init[j];
-    st->since_best = 0;
-    st->best_rel = -1.0;
   }
 }
 
@@ -78,8 +77,11 @@ size_t batch_smem_bytes(unsigned budget) { return (size_t)budget + SMEM_RESERVE;
 }  // namespace nmfgb
 
 struct nmf_batch {
-  std::vector<nmf_handle*> h;
+  std::vector<nmf_handle*> h;          // problem slots (null: free)
   std::vector<nmf_config> cfg;
+  std::vector<char> active;            // slots included in the sweeps
+  std::vector<int> plan_idx;           // slots of the current plan, in plan order
+  int sts_cap = 0;                     // capacity of dSts / dPassInit
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int nsm = 0, smem_optin = 0;
@@ -153,7 +155,10 @@ nmf_status build_plan(nmf_batch* b) {
   std::map<std::pair<int, int>, int> index;
   std::vector<std::vector<BatchProb>> hp;
   double total_work = 0.0;
+  b->plan_idx.clear();
   for (int j = 0; j < np; ++j) {
+    if (!b->h[j] || !b->active[j]) continue;
+    b->plan_idx.push_back(j);
     HandleInfo hi;
     handle_info(b->h[j], &hi);
     if (!hi.factors_set) return bfail(b, NMF_ESTATE, "problem " + std::to_string(j) + ": factors not set");
@@ -239,6 +244,24 @@ nmf_status build_plan(nmf_batch* b) {
     a.force_var = b->force_var;
     a.smem_budget = budget;
   }
+  // control blocks of the plan's problems, in plan order
+  const int npl = (int)b->plan_idx.size();
+  if (npl > b->sts_cap) {
+    cudaFree(b->dSts);
+    cudaFree(b->dPassInit);
+    b->dSts = nullptr;
+    b->dPassInit = nullptr;
+    BCUDA(b, cudaMalloc(&b->dSts, sizeof(DevState*) * npl));
+    BCUDA(b, cudaMalloc(&b->dPassInit, sizeof(int) * npl));
+    b->sts_cap = npl;
+  }
+  std::vector<DevState*> sts(npl);
+  for (int i = 0; i < npl; ++i) {
+    HandleInfo hi;
+    handle_info(b->h[b->plan_idx[i]], &hi);
+    sts[i] = hi.dSt;
+  }
+  if (npl) BCUDA(b, cudaMemcpy(b->dSts, sts.data(), sizeof(DevState*) * npl, cudaMemcpyHostToDevice));
   b->plan_valid = true;
   return NMF_OK;
 }
@@ -282,7 +305,7 @@ nmf_status enqueue_sweeps(nmf_batch* b, int nsweeps) {
     }
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
   }
-  batch_count_kernel<<<1, 256, 0, b->stream>>>(b->dSts, (int)b->h.size(), b->dDone);
+  batch_count_kernel<<<1, 256, 0, b->stream>>>(b->dSts, (int)b->plan_idx.size(), b->dDone);
   BCUDA(b, cudaGetLastError());
   return NMF_OK;
 }
@@ -317,6 +340,76 @@ nmf_status run_chunk(nmf_batch* b, int nsweeps) {
 
 }  // namespace
 
+namespace nmfgb {
+
+nmf_status batch_create_empty(void* cuda_stream, nmf_batch** out) {
+  *out = nullptr;
+  nmf_batch* b = new nmf_batch();
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    delete b;
+    return NMF_ECUDA;
+  }
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  bool ok = true;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    ok &= cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess;
+    b->own_stream = ok;
+  }
+  ok &= cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaMalloc(&b->dDone, sizeof(int)) == cudaSuccess;
+  ok &= cudaMallocHost(&b->hDone, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    nmf_batch_destroy(b);
+    return NMF_ECUDA;
+  }
+  *out = b;
+  return NMF_OK;
+}
+
+nmf_status batch_add(nmf_batch* b, const nmf_config& cfg, int* slot) {
+  nmf_config c = cfg;
+  c.cuda_stream = b->stream;   // every problem's work is ordered with the batch launches
+  nmf_handle* h = nullptr;
+  nmf_status s = nmf_create(&c, &h);
+  if (s != NMF_OK) return s;
+  int j = 0;
+  while (j < (int)b->h.size() && b->h[j]) ++j;
+  if (j == (int)b->h.size()) {
+    b->h.push_back(nullptr);
+    b->cfg.emplace_back();
+    b->active.push_back(0);
+  }
+  b->h[j] = h;
+  b->cfg[j] = c;
+  b->active[j] = 1;
+  b->plan_valid = false;
+  *slot = j;
+  return NMF_OK;
+}
+
+void batch_remove(nmf_batch* b, int j) {
+  if (j < 0 || j >= (int)b->h.size() || !b->h[j]) return;
+  cudaStreamSynchronize(b->stream);
+  nmf_destroy(b->h[j]);
+  b->h[j] = nullptr;
+  b->active[j] = 0;
+  b->plan_valid = false;
+}
+
+void batch_set_active(nmf_batch* b, int j, bool on) {
+  if (j < 0 || j >= (int)b->h.size() || !b->h[j]) return;
+  if ((b->active[j] != 0) != on) b->plan_valid = false;
+  b->active[j] = on ? 1 : 0;
+}
+
+cudaStream_t batch_stream(nmf_batch* b) { return b->stream; }
+
+}  // namespace nmfgb
+
 extern "C" {
 
 nmf_status nmf_batch_create(const nmf_config* cfgs, int32_t nprob, void* cuda_stream, nmf_batch** out) {
@@ -325,40 +418,17 @@ nmf_status nmf_batch_create(const nmf_config* cfgs, int32_t nprob, void* cuda_st
   for (int j = 0; j < nprob; ++j)
     if (cfgs[j].prec != NMF_PREC_MIXED || cfgs[j].k < 1 || (cfgs[j].k > 8 && cfgs[j].k != 16))
       return NMF_EINVAL;
-  nmf_batch* b = new nmf_batch();
-  auto bail = [&](nmf_status s) {
-    nmf_batch_destroy(b);
-    return s;
-  };
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return bail(NMF_ECUDA);
-  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&b->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (cuda_stream) {
-    b->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(NMF_ECUDA);
-    b->own_stream = true;
-  }
-  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return bail(NMF_ECUDA);
-  b->cfg.assign(cfgs, cfgs + nprob);
-  b->h.assign(nprob, nullptr);
-  std::vector<DevState*> sts(nprob);
+  nmf_batch* b = nullptr;
+  nmf_status s = batch_create_empty(cuda_stream, &b);
+  if (s != NMF_OK) return s;
   for (int j = 0; j < nprob; ++j) {
-    nmf_config c = cfgs[j];
-    c.cuda_stream = b->stream;   // every problem's work is ordered with the batch launches
-    nmf_status s = nmf_create(&c, &b->h[j]);
-    if (s != NMF_OK) return bail(s);
-    HandleInfo hi;
-    handle_info(b->h[j], &hi);
-    sts[j] = hi.dSt;
+    int slot = -1;
+    s = batch_add(b, cfgs[j], &slot);
+    if (s != NMF_OK) {
+      nmf_batch_destroy(b);
+      return s;
+    }
   }
-  if (cudaMalloc(&b->dSts, sizeof(DevState*) * nprob) != cudaSuccess) return bail(NMF_ENOMEM);
-  if (cudaMalloc(&b->dPassInit, sizeof(int) * nprob) != cudaSuccess) return bail(NMF_ENOMEM);
-  if (cudaMalloc(&b->dDone, sizeof(int)) != cudaSuccess) return bail(NMF_ENOMEM);
-  if (cudaMallocHost(&b->hDone, sizeof(int)) != cudaSuccess) return bail(NMF_ENOMEM);
-  if (cudaMemcpy(b->dSts, sts.data(), sizeof(DevState*) * nprob, cudaMemcpyHostToDevice) != cudaSuccess)
-    return bail(NMF_ECUDA);
   *out = b;
   return NMF_OK;
 }
@@ -367,7 +437,8 @@ nmf_status nmf_batch_destroy(nmf_batch* b) {
   if (!b) return NMF_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
   free_plan(b);
-  for (nmf_handle* h : b->h) nmf_destroy(h);
+  for (nmf_handle* h : b->h)
+    if (h) nmf_destroy(h);
   cudaFree(b->dSts);
   cudaFree(b->dPassInit);
   cudaFree(b->dDone);
@@ -382,12 +453,12 @@ int32_t nmf_batch_size(const nmf_batch* b) { return b ? (int32_t)b->h.size() : 0
 
 nmf_handle* nmf_batch_problem(nmf_batch* b, int32_t j) {
   if (!b || j < 0 || j >= (int32_t)b->h.size()) return nullptr;
-  return b->h[j];
+  return b->h[j];   // null for a free slot
 }
 
 nmf_status nmf_batch_append_columns(nmf_batch* b, int32_t j, const void* cols, int64_t ncols, int64_t ld,
                                     int32_t dtype, int32_t on_device) {
-  if (!b || j < 0 || j >= (int32_t)b->h.size()) return NMF_EINVAL;
+  if (!b || j < 0 || j >= (int32_t)b->h.size() || !b->h[j]) return NMF_EINVAL;
   if (b->poisoned) return b->poisoned;
   b->plan_valid = false;
   return nmf_append_columns(b->h[j], cols, ncols, ld, dtype, on_device);
@@ -395,7 +466,7 @@ nmf_status nmf_batch_append_columns(nmf_batch* b, int32_t j, const void* cols, i
 
 nmf_status nmf_batch_set_factors(nmf_batch* b, int32_t j, const double* X, const double* Y,
                                  int32_t on_device) {
-  if (!b || j < 0 || j >= (int32_t)b->h.size()) return NMF_EINVAL;
+  if (!b || j < 0 || j >= (int32_t)b->h.size() || !b->h[j]) return NMF_EINVAL;
   if (b->poisoned) return b->poisoned;
   b->plan_valid = false;
   return nmf_set_factors(b->h[j], X, Y, on_device);
@@ -403,7 +474,7 @@ nmf_status nmf_batch_set_factors(nmf_batch* b, int32_t j, const double* X, const
 
 nmf_status nmf_batch_get_factors(nmf_batch* b, int32_t j, double* X, double* Y, uint32_t* xmask,
                                  uint32_t* ymask, int32_t on_device) {
-  if (!b || j < 0 || j >= (int32_t)b->h.size()) return NMF_EINVAL;
+  if (!b || j < 0 || j >= (int32_t)b->h.size() || !b->h[j]) return NMF_EINVAL;
   if (b->poisoned) return b->poisoned;
   return nmf_get_factors(b->h[j], X, Y, xmask, ymask, on_device);
 }
@@ -427,24 +498,29 @@ nmf_status nmf_batch_set_schedule(nmf_batch* b, int32_t cols_per_item, int32_t s
 nmf_status nmf_batch_sweep(nmf_batch* b, int32_t max_sweeps, nmf_stats* stats, int32_t* sweeps_run) {
   if (!b || max_sweeps < 0) return NMF_EINVAL;
   if (b->poisoned) return b->poisoned;
-  const int np = (int)b->h.size();
   if (!b->plan_valid) {
     nmf_status s = build_plan(b);
     if (s != NMF_OK) return s;
   }
+  const int np = (int)b->plan_idx.size();
+  if (np == 0) {
+    if (sweeps_run) *sweeps_run = 0;
+    return NMF_OK;
+  }
   int cap = max_sweeps;
   if (cap == 0)
-    for (const nmf_config& c : b->cfg) cap = std::max(cap, std::max(1, (int)c.max_sweeps));
+    for (int jj : b->plan_idx) cap = std::max(cap, std::max(1, (int)b->cfg[jj].max_sweeps));
   // resume every problem: its schedule phase, and the iterate index before the call
   std::vector<int> pass_init(np), iter0(np), fp0(np);
-  for (int j = 0; j < np; ++j) {
+  for (int i = 0; i < np; ++i) {
+    const int j = b->plan_idx[i];
     nmf_status s = handle_sync_state(b->h[j]);
     if (s != NMF_OK) return bfail(b, s, "problem " + std::to_string(j) + ": state");
     HandleInfo hi;
     handle_info(b->h[j], &hi);
-    iter0[j] = hi.hSt->iter;
-    fp0[j] = hi.hSt->fp64_sweeps;
-    pass_init[j] = (b->force_var == 1 || (b->force_var < 0 && hi.phase == 1)) ? VAR_DF : VAR_F32;
+    iter0[i] = hi.hSt->iter;
+    fp0[i] = hi.hSt->fp64_sweeps;
+    pass_init[i] = (b->force_var == 1 || (b->force_var < 0 && hi.phase == 1)) ? VAR_DF : VAR_F32;
   }
   BCUDA(b, cudaMemcpyAsync(b->dPassInit, pass_init.data(), sizeof(int) * np, cudaMemcpyHostToDevice, b->stream));
   batch_reset_kernel<<<(np + 255) / 256, 256, 0, b->stream>>>(b->dSts, b->dPassInit, np);
@@ -465,7 +541,8 @@ nmf_status nmf_batch_sweep(nmf_batch* b, int32_t max_sweeps, nmf_stats* stats, i
     }
   }
   nmf_status worst = NMF_OK;
-  for (int j = 0; j < np; ++j) {
+  for (int i = 0; i < np; ++i) {
+    const int j = b->plan_idx[i];
     nmf_status s = handle_sync_state(b->h[j]);
     HandleInfo hi;
     handle_info(b->h[j], &hi);
@@ -475,10 +552,10 @@ nmf_status nmf_batch_sweep(nmf_batch* b, int32_t max_sweeps, nmf_stats* stats, i
     if (stats) {
       const int it = hi.hSt->iter;
       const bool stop_kkt = hi.hSt->done && hi.hSt->stop_reason == 1;
-      const int worked = (it - iter0[j]) + (stop_kkt ? 1 : 0);
+      const int worked = (it - iter0[i]) + (stop_kkt ? 1 : 0);
       const int measured = stop_kkt ? it : it - 1;
       handle_fill_stats(b->h[j], measured, worked, -1, &stats[j]);
-      stats[j].fp64_sweeps = hi.hSt->fp64_sweeps - fp0[j];
+      stats[j].fp64_sweeps = hi.hSt->fp64_sweeps - fp0[i];
     }
   }
   if (sweeps_run) *sweeps_run = done_sweeps;
@@ -512,11 +589,11 @@ nmf_status nmf_batch_autotune(nmf_batch* b, int32_t trial_sweeps, int32_t* cols_
       b->plan_valid = false;
       nmf_status s = build_plan(b);
       if (s != NMF_OK) continue;
-      std::vector<int> pass_init(b->h.size(), VAR_F32);
+      std::vector<int> pass_init(b->plan_idx.size(), VAR_F32);
       BCUDA(b, cudaMemcpyAsync(b->dPassInit, pass_init.data(), sizeof(int) * pass_init.size(),
                                cudaMemcpyHostToDevice, b->stream));
-      batch_reset_kernel<<<((int)b->h.size() + 255) / 256, 256, 0, b->stream>>>(b->dSts, b->dPassInit,
-                                                                                (int)b->h.size());
+      batch_reset_kernel<<<((int)pass_init.size() + 255) / 256, 256, 0, b->stream>>>(
+          b->dSts, b->dPassInit, (int)pass_init.size());
       s = enqueue_sweeps(b, 1);   // warm-up (attributes, caches)
       if (s != NMF_OK) return s;
       BCUDA(b, cudaEventRecord(e0, b->stream));

@@ -51,7 +51,7 @@ struct DevState {
   double stats[STAT_CAP][NSTAT];
   double xiter[2][NXT];     // X-half terms of the iterate held in buffers 0 / 1
   double msq;               // ||M||_F^2 of the resident window
-  double best_rel;          // device-driven mixed schedule: best FP32-pass relative KKT (< 0: none)
+  double best_rel;          // device-driven mixed schedule: best FP32-pass relative KKT (<= 0: none)
 };
 
 // Arithmetic of one M pass.

@@ -28,4 +28,15 @@ void handle_set_phase(nmf_handle* h, int phase);
 void handle_fill_stats(nmf_handle* h, int measured, int sweeps, int fp64_sweeps, nmf_stats* out);
 nmf_status handle_fail(nmf_handle* h, nmf_status s, const char* msg);
 
+// device bytes nmf_create allocates for one problem (admission by footprint)
+int64_t handle_footprint(int64_t n, int k, int64_t mcap, bool store_f32, int nsm);
+
+// dynamic membership of a batch (the streaming server): slots are created
+// on admission and destroyed on close; inactive slots are left out of sweeps
+nmf_status batch_create_empty(void* cuda_stream, nmf_batch** out);
+nmf_status batch_add(nmf_batch* b, const nmf_config& cfg, int* slot);
+void batch_remove(nmf_batch* b, int j);
+void batch_set_active(nmf_batch* b, int j, bool on);
+cudaStream_t batch_stream(nmf_batch* b);
+
 }  // namespace nmfgb

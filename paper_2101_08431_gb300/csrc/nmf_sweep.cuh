@@ -1033,7 +1033,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       if (p.fp64_pass) ++st->fp64_sweeps;
       if (p.auto_mixed && st->pass_var != VAR_DF && rec[ST_VALID] > 0.0) {
         const double rel = rec[ST_REL];
-        if (st->best_rel < 0.0 || rel < 0.98 * st->best_rel) {
+        if (st->best_rel <= 0.0 || rel < 0.98 * st->best_rel) {   // <= 0: none yet
           st->best_rel = rel;
           st->since_best = 0;
         } else {

@@ -74,6 +74,21 @@ def test_batch_arguments_rejected_before_any_device_work(lib):
     assert lib.nmf_batch_destroy(None) == _native.NMF_OK
 
 
+def test_server_arguments_rejected_before_any_device_work(lib):
+    from paper_2101_08431_gb300 import _native
+    cfg = _native.nmf_server_config()
+    lib.nmf_server_config_init(C.byref(cfg))
+    assert cfg.max_streams == 64 and cfg.sweeps_per_round == 8 and cfg.kkt_target == 1e-6
+    s = C.c_void_p()
+    assert lib.nmf_server_create(None, C.byref(s)) == _native.NMF_EINVAL
+    cfg.sweeps_per_round = 0
+    assert lib.nmf_server_create(C.byref(cfg), C.byref(s)) == _native.NMF_EINVAL
+    i = C.c_int32()
+    assert lib.nmf_server_open_stream(None, 100, 3, 10, 0, C.byref(i)) == _native.NMF_EINVAL
+    assert lib.nmf_server_submit(None, 0, None, 1, 100, None) == _native.NMF_EINVAL
+    assert lib.nmf_server_destroy(None) == _native.NMF_OK
+
+
 def test_library_is_built_for_sm_103a_only():
     from paper_2101_08431_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
