@@ -496,17 +496,34 @@ def serving_leg(args, rank, sptr):
 
 def run_ncu_case(args):
     """A short, fixed launch sequence for ncu captures: priming, PRECOND_NCU
-    sweeps of the chosen pass, then 3 more (capture them with -s/-c)."""
+    sweeps of the chosen pass, then 3 more (capture them with -s/-c).
+    "batch": 16 problems of the batched workload, 3 FP32-pass sweeps in one
+    plain persistent launch per class."""
     import torch
-    from paper_2101_08431_gb300 import NMF_PREC_FP64, NMF_PREC_MIXED, StreamingNMF, build
+    from paper_2101_08431_gb300 import NMF_PREC_FP64, NMF_PREC_MIXED, StreamingNMF, StreamingNMFBatch, build
     build.build()
+    if args.ncu_case == "batch":
+        import synth
+        shapes = synth.batch_problem_shapes(16)
+        b = StreamingNMFBatch([(n, k, m) for n, m, k, _ in shapes], kkt_target=0.0)
+        for j, (n, m, k, seed) in enumerate(shapes):
+            M, _, _ = synth.pdf_like(n, m, k, noise=NOISE, relative=True, seed=seed)
+            X, Y = synth.init_factors(n, m, k, seed=seed)
+            b.append_columns(j, np.asfortranarray(M, dtype=np.float32))
+            b.set_factors(j, X, Y)
+        b.set_pass_mode(0)
+        b.sweep(3)
+        torch.cuda.synchronize()
+        b.close()
+        print("ncu case batch: 16 problems, 3 sweeps")
+        return 0
     M32, M64, X0, Y0 = make_data(0)
     fp64 = args.ncu_case == "f64"
     h = StreamingNMF(N_ROWS, RANK_K, M_COLS, prec=NMF_PREC_FP64 if fp64 else NMF_PREC_MIXED, kkt_target=0.0)
     h.append_columns(M64 if fp64 else M32)
     h.set_factors(X0, Y0)
     if not fp64:
-        h.set_pass_mode(1 if args.ncu_case == "ref" else 0)
+        h.set_pass_mode({"ref": 1, "df": 2}.get(args.ncu_case, 0))
     h.sweep(args.ncu_precond + 3, want_stats=False)
     torch.cuda.synchronize()
     h.close()
@@ -527,7 +544,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--batch-ttk", action="store_true",
                     help="also run every batched problem to relative KKT 1e-8")
-    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64"], default=None,
+    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "batch"], default=None,
                     help="run only a short launch sequence for an ncu capture")
     ap.add_argument("--ncu-precond", type=int, default=200)
     args = ap.parse_args()

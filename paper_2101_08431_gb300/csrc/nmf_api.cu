@@ -179,6 +179,14 @@ struct nmf_handle {
   KernelSet ks[NVAR]{};
   bool has[NVAR] = {false, false, false, false};
   int max_clusters[NVAR][4] = {};   // per variant, cluster size 1, 2, 4, 8 (full smem)
+  // CUDA graph of one chunk of sweeps per variant, keyed by the ring state
+  // it was captured with (m, head); a signature is first run uncaptured
+  struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    int m = -1, head = -1;         // signature of exec
+    int seen_m = -1, seen_head = -1;   // last signature run uncaptured
+  };
+  ChunkGraph graphs[NVAR];
   // per-kernel timing (event triplets around each sweep's two launches)
   bool timing = false;
   static constexpr int NEV = 512;
@@ -321,6 +329,52 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode) {
   return NMF_OK;
 }
 
+// CHUNK sweeps of variant var: replay of the captured graph when its
+// signature matches, otherwise plain launches (captured the second time the
+// same signature is seen).
+nmf_status launch_chunk(nmf_handle* h, int var, int chunk) {
+  nmf_handle::ChunkGraph& g = h->graphs[var];
+  const bool graphable = !h->timing && chunk == CHUNK;
+  if (graphable && g.exec && g.m == h->m && g.head == h->head) {
+    CUDA_TRY(h, cudaGraphLaunch(g.exec, h->stream));
+    h->launches += 2 * chunk;
+    return NMF_OK;
+  }
+  if (graphable && g.seen_m == h->m && g.seen_head == h->head) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    nmf_status s = NMF_OK;
+    const int64_t l0 = h->launches;
+    for (int i = 0; i < chunk && s == NMF_OK; ++i) s = launch_pair(h, var, MODE_SWEEP);
+    h->launches = l0;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (s != NMF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(h, NMF_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) return fail(h, NMF_ECUDA, std::string("sweep graph: ") + cudaGetErrorString(e2));
+    g.m = h->m;
+    g.head = h->head;
+    CUDA_TRY(h, cudaGraphLaunch(g.exec, h->stream));
+    h->launches += 2 * chunk;
+    return NMF_OK;
+  }
+  for (int i = 0; i < chunk; ++i) {
+    nmf_status s = launch_pair(h, var, MODE_SWEEP);
+    if (s != NMF_OK) return s;
+  }
+  if (graphable) {
+    g.seen_m = h->m;
+    g.seen_head = h->head;
+  }
+  return NMF_OK;
+}
+
 int variant_for(const nmf_handle* h) {
   if (!h->store_f32) return VAR_F64;
   if (h->forced_mode == 0) return VAR_F32;
@@ -404,6 +458,8 @@ int64_t nmf_num_columns(const nmf_handle* h) { return h ? h->m : 0; }
 nmf_status nmf_destroy(nmf_handle* h) {
   if (!h) return NMF_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (int i = 0; i < nmf_handle::NEV; ++i)
     for (int j = 0; j < 3; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
@@ -714,10 +770,8 @@ nmf_status nmf_sweep(nmf_handle* h, int32_t nsweeps, nmf_stats* stats) {
   while (launched < cap) {
     const int chunk = need_checks ? std::min(CHUNK, cap - launched) : cap - launched;
     const int var = variant_for(h);
-    for (int i = 0; i < chunk; ++i) {
-      s = launch_pair(h, var, MODE_SWEEP);
-      if (s != NMF_OK) return s;
-    }
+    s = launch_chunk(h, var, chunk);
+    if (s != NMF_OK) return s;
     launched += chunk;
     if (!need_checks) {
       h->snap_valid = false;

@@ -37,6 +37,7 @@ cudaError_t launch_y(const Problem& p, int mode, const YPlan& L, cudaStream_t s)
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_done[dev] = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -89,9 +90,14 @@ cudaError_t launch_x(const Problem& p, int mode, int Q, int nxblk, cudaStream_t 
   static bool attr_done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dyn > 48 * 1024 && dev >= 0 && dev < 64 && !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    if (dyn > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+    }
+    // the same shared-memory carve-out as the M pass, so that the SMs need
+    // not be reconfigured between the two kernels of a sweep
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_done[dev] = true;
   }
   kern<<<nxblk, XTraits<K>::T, dyn, s>>>(p, mode, Q, nxblk);
