@@ -650,6 +650,41 @@ __device__ void tree_sum(const double* src, int nparts, size_t stride, int nval,
   }
 }
 
+// Two tree_sum reductions in one pass (values [0, n1) from src1, then
+// [n1, n1 + n2) from src2), so that both sets of loads are in flight at
+// once; every value is summed in the same order as by tree_sum.
+template <int T>
+__device__ void tree_sum2(const double* src1, int np1, size_t st1, int n1, double* out1, int max1,
+                          const double* src2, int np2, size_t st2, int n2, double* out2, int max2) {
+  constexpr int G = 8, VPB = T / G, U = 8;
+  const int g = threadIdx.x & (G - 1), vi = threadIdx.x / G;
+  for (int e0 = 0; e0 < n1 + n2; e0 += VPB) {
+    const int e = e0 + vi;
+    const bool ok = e < n1 + n2, first = e < n1;
+    const double* src = first ? src1 : src2;
+    const int np = first ? np1 : np2, ee = first ? e : e - n1;
+    const size_t stride = first ? st1 : st2;
+    const bool is_max = ok && ee == (first ? max1 : max2);
+    double r = 0.0;
+    for (int q0 = g; q0 < (ok ? np : 0); q0 += G * U) {
+      double w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * G;
+        w[u] = q < np ? src[(size_t)q * stride + ee] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) r = is_max ? dmax_nn(r, w[u]) : r + w[u];
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, r, o);
+      r = is_max ? dmax_nn(r, w) : r + w;
+    }
+    if (ok && g == 0) (first ? out1 : out2)[ee] = r;
+  }
+}
+
 // Dynamic shared memory of the row pass: the working arrays, then the
 // subset table of H (k <= 8).
 template <typename TA, int K>
@@ -657,6 +692,15 @@ struct XSmem {
   using Tr = XTraits<K>;
   static constexpr bool TABLE = K <= 8;
   static constexpr int NWN = TABLE ? Tr::RB / LaneGroup<K>::CPW : 1;   // NNLS warps (k <= 8)
+  // warps that build the subset table of H: enough lane groups for its
+  // largest level (C(k, k/2) subsets), at most half the block
+  static constexpr int binom_mid() {
+    int v = 1;
+    for (int i = 1; i <= K / 2; ++i) v = v * (K - K / 2 + i) / i;
+    return v;
+  }
+  static constexpr int WT_NEED = (binom_mid() * LaneGroup<K>::KP + 31) / 32;
+  static constexpr int WT = TABLE ? (WT_NEED < 1 ? 1 : (WT_NEED > Tr::NW / 2 ? Tr::NW / 2 : WT_NEED)) : 0;
   struct Small {
     double H[K * K];
     double Gs[K * K];
@@ -729,18 +773,30 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     }
     samples[tid] = msk;
   }
-  {
+  // the first wt warps build the subset table of H while the others sum the
+  // cluster partials of P
+  const int wt = (TABLE && !hglob && mode == MODE_SWEEP) ? Xs::WT : 0;
+  const int npw = NW - wt;
+  if (wt) __syncthreads();   // H
+  if (warp < wt) {
+    if constexpr (TABLE) {
+      NnlsSolver<K> ts;
+      ts.init(H, 2.220446049250313e-16);
+      build_subset_table_lanes<K>(ts, tab, tok, 0, wt * 32, [wt] { named_sync(2, wt * 32); });
+    }
+  } else {
     using PO = PartOps<TA>;
     const TA* Pp = static_cast<const TA*>(p.Ppart);
+    const int pw = warp - wt;
     TA acc[K];
 #pragma unroll
     for (int a = 0; a < K; ++a) acc[a] = PO::zero();
     if (active)
-      for (int q0 = warp; q0 < Q; q0 += NW * 4) {   // four partials in flight per thread
+      for (int q0 = pw; q0 < Q; q0 += npw * 4) {   // four partials in flight per thread
         TA w[4][K];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int qq = q0 + u * NW;
+          const int qq = q0 + u * npw;
 #pragma unroll
           for (int a = 0; a < K; ++a) w[u][a] = qq < Q ? Pp[((size_t)qq * p.ld + row) * K + a] : PO::zero();
         }
@@ -750,17 +806,13 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
           for (int a = 0; a < K; ++a) acc[a] = PO::add(acc[a], w[u][a]);
       }
 #pragma unroll
-    for (int a = 0; a < K; ++a) psum[warp][lane][a] = acc[a];
+    for (int a = 0; a < K; ++a) psum[pw][lane][a] = acc[a];
   }
   __syncthreads();
   NnlsSolver<K> solver;
   solver.init(H, 2.220446049250313e-16);
-  if (mode == MODE_SWEEP) {
-    if constexpr (TABLE) {
-      if (!hglob) build_subset_table_lanes<K>(solver, tab, tok, 0, T, [] { __syncthreads(); });
-    } else {
-      build_cache<K>(&cache, solver, samples, CACHE_N);
-    }
+  if constexpr (!TABLE) {
+    if (mode == MODE_SWEEP) build_cache<K>(&cache, solver, samples, CACHE_N);
   }
 
   if (TABLE) {
@@ -782,8 +834,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       uint32_t old_mask = 0;
       if (comp) {
         TA ts = psum[0][lrow][g.a];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][g.a]);
+        for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][g.a]);
         pr = PartOps<TA>::to_double(ts);
         xo = p.X[cur][(size_t)grow_i * K + g.a];
       }
@@ -904,8 +955,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
 #pragma unroll
       for (int a = 0; a < K; ++a) {
         TA ts = psum[0][lane][a];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) ts = PartOps<TA>::add(ts, psum[w][lane][a]);
+        for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lane][a]);
         pr[a] = PartOps<TA>::to_double(ts);
         xo[a] = p.X[cur][(size_t)row * K + a];
         xn[a] = xo[a];
@@ -995,8 +1045,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   __syncthreads();
   if (ticket != (unsigned)(nxblk - 1)) return;
   __threadfence();
-  tree_sum<T>(p.Xpart, nxblk, NV, NV, fin, K * K + XT_XMAX);
-  tree_sum<T>(p.Yterms, Q, NYT, NYT, yfin, YT_YMAX);
+  tree_sum2<T>(p.Xpart, nxblk, NV, NV, fin, K * K + XT_XMAX, p.Yterms, Q, NYT, NYT, yfin, YT_YMAX);
   __syncthreads();
   if (tid < K * K) {
     p.G[tid] = fin[tid];
