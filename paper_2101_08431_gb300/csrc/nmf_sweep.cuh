@@ -232,25 +232,46 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         if (mode != MODE_KKT) {
           const int tj = min(TJ, ncols - u * TJ);
           const TM* tile = stages + (size_t)(u % S) * TJ * R;
+          if constexpr (PSM) {
+            // accumulators in shared memory: a row loop unrolled twice keeps
+            // the (long, compensated) body small for the instruction cache
+            // and still gives 2 K independent chains; the tile's y values are
+            // staged once
+            VT yv[TJ][K];
 #pragma unroll
-          for (int r = 0; r < RPT; ++r) {
-            const int rr = tid + r * TC;
-            if (rr < rows_c) {
+            for (int jj = 0; jj < TJ; ++jj)
+#pragma unroll
+              for (int a = 0; a < K; ++a) yv[jj][a] = sm.ybufA[ub][jj][a];
+#pragma unroll 2
+            for (int rr = tid; rr < rows_c; rr += TC) {
               AT pa[K];
 #pragma unroll
-              for (int a = 0; a < K; ++a) pa[a] = PSM ? ps[(size_t)a * R + rr] : pacc[PSM ? 0 : r][a];
+              for (int a = 0; a < K; ++a) pa[a] = ps[(size_t)a * R + rr];
 #pragma unroll
               for (int jj = 0; jj < TJ; ++jj) {
                 if (jj < tj) {
                   const TM mv = tile[(size_t)jj * R + rr];
 #pragma unroll
-                  for (int a = 0; a < K; ++a) pa[a] = AR::madd(mv, sm.ybufA[ub][jj][a], pa[a]);
+                  for (int a = 0; a < K; ++a) pa[a] = AR::madd(mv, yv[jj][a], pa[a]);
                 }
               }
 #pragma unroll
-              for (int a = 0; a < K; ++a) {
-                if constexpr (PSM) ps[(size_t)a * R + rr] = pa[a];
-                else pacc[PSM ? 0 : r][a] = pa[a];
+              for (int a = 0; a < K; ++a) ps[(size_t)a * R + rr] = pa[a];
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+              const int rr = tid + r * TC;
+              if (rr < rows_c) {
+#pragma unroll
+                for (int jj = 0; jj < TJ; ++jj) {
+                  if (jj < tj) {
+                    const TM mv = tile[(size_t)jj * R + rr];
+#pragma unroll
+                    for (int a = 0; a < K; ++a)
+                      pacc[PSM ? 0 : r][a] = AR::madd(mv, sm.ybufA[ub][jj][a], pacc[PSM ? 0 : r][a]);
+                  }
+                }
               }
             }
           }
