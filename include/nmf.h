@@ -291,6 +291,14 @@ nmf_status nmf_batch_sweep(nmf_batch *b, int32_t max_sweeps, nmf_stats *stats, i
 nmf_status nmf_batch_autotune(nmf_batch *b, int32_t trial_sweeps, int32_t *cols_per_item, int32_t *stage_cap,
                               double *best_ms_per_sweep);
 
+/* Self-test of the bounded device wait used by the batched form's dependency
+ * counters: one kernel waits, with a limit of `polls` polls (~256 ns each,
+ * 1..2^24), on a counter that nothing increments.  Returns NMF_ETIMEOUT when
+ * the wait gave up and reported it through the control block (the expected
+ * outcome), NMF_OK if the wait ended otherwise, NMF_EINVAL for a bad limit.
+ * The paper has no counterpart; no kernel of the library spins unbounded. */
+nmf_status nmf_selftest_bounded_wait(int64_t polls, void *cuda_stream);
+
 /* Kernel launches issued by the batch (graph replays count their launches). */
 int64_t nmf_batch_launch_count(const nmf_batch *b);
 const char *nmf_batch_last_error(const nmf_batch *b);

@@ -36,6 +36,12 @@ __global__ void batch_reset_kernel(DevState* const* sts, const int* pass_init, i
   }
 }
 
+// Self-test of the bounded dependency wait: thread 0 waits on a counter that
+// nothing increments, with the given poll limit, exactly as a batch item does.
+__global__ void wait_selftest_kernel(const unsigned* ctr, DevState* st, long long polls) {
+  if (threadIdx.x == 0) batch_wait(ctr, 1u, st, polls);
+}
+
 // number of problems that have stopped
 __global__ void batch_count_kernel(DevState* const* sts, int n, int* out) {
   __shared__ int c;
@@ -622,6 +628,31 @@ nmf_status nmf_batch_autotune(nmf_batch* b, int32_t trial_sweeps, int32_t* cols_
   if (stage_cap) *stage_cap = bs;
   if (best_ms_per_sweep) *best_ms_per_sweep = best;
   return NMF_OK;
+}
+
+nmf_status nmf_selftest_bounded_wait(int64_t polls, void* cuda_stream) {
+  if (polls < 1 || polls > (int64_t(1) << 24)) return NMF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned* ctr = nullptr;
+  DevState* st = nullptr;
+  DevState hst;
+  if (cudaMalloc(&ctr, sizeof(unsigned)) != cudaSuccess) return NMF_ENOMEM;
+  if (cudaMalloc(&st, sizeof(DevState)) != cudaSuccess) {
+    cudaFree(ctr);
+    return NMF_ENOMEM;
+  }
+  nmf_status out = NMF_ECUDA;
+  if (cudaMemsetAsync(ctr, 0, sizeof(unsigned), s) == cudaSuccess &&
+      cudaMemsetAsync(st, 0, sizeof(DevState), s) == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(ctr, st, (long long)polls);
+    if (cudaGetLastError() == cudaSuccess &&
+        cudaMemcpyAsync(&hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess)
+      out = (hst.err & ERR_TIMEOUT) && hst.done ? NMF_ETIMEOUT : NMF_OK;
+  }
+  cudaFree(ctr);
+  cudaFree(st);
+  return out;
 }
 
 int64_t nmf_batch_launch_count(const nmf_batch* b) { return b ? b->launches : 0; }

@@ -60,8 +60,9 @@ constexpr long long BATCH_SPIN_LIMIT = 1ll << 23;   // polls of ~256 ns: about 2
 
 // Thread 0: wait until *ctr >= target or the problem has stopped.  On
 // timeout the problem is marked stopped with ERR_TIMEOUT.
-__device__ __forceinline__ void batch_wait(const unsigned* ctr, unsigned target, DevState* st) {
-  for (long long i = 0; i < BATCH_SPIN_LIMIT; ++i) {
+__device__ __forceinline__ void batch_wait(const unsigned* ctr, unsigned target, DevState* st,
+                                           long long limit = BATCH_SPIN_LIMIT) {
+  for (long long i = 0; i < limit; ++i) {
     if (ld_acquire_u32(ctr) >= target) return;
     if (*reinterpret_cast<volatile int*>(&st->done)) return;
     __nanosleep(256);
@@ -75,15 +76,23 @@ __device__ __forceinline__ void batch_wait(const unsigned* ctr, unsigned target,
 // cluster partials (the same fixed-order tree as the row pass), and its
 // subset table, into the problem's global buffers; every row block of the
 // sweep then reads them instead of forming them itself.  All 512 threads.
-template <int K>
+// The table is in the value type of the sweep's row solves (NV: FP32 for the
+// FP32 pass), stored in the problem's table buffer.
+template <int K, typename NV>
 __device__ void batch_h_stage(const Problem& p, int Q, unsigned char* smem_raw) {
   double* H = reinterpret_cast<double*>(smem_raw);
+  NV* Hn = reinterpret_cast<NV*>(smem_raw + 2048);
   tree_sum<512>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
   __syncthreads();
-  for (int e = threadIdx.x; e < K * K; e += 512) p.Hg[e] = H[e];
+  for (int e = threadIdx.x; e < K * K; e += 512) {
+    p.Hg[e] = H[e];
+    Hn[e] = (NV)H[e];
+  }
+  __syncthreads();
   NnlsSolver<K> solver;
   solver.init(H, 2.220446049250313e-16);
-  build_subset_table_lanes<K>(solver, p.Htab, p.Hok, 0, 512, [] { __syncthreads(); });
+  build_subset_table_lanes_v<K, NV>(Hn, (NV)solver.pivot_min, reinterpret_cast<NV*>(p.Htab), p.Hok, 0, 512,
+                                    [] { __syncthreads(); });
 }
 
 template <int K>
@@ -134,7 +143,8 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs a) {
         __syncthreads();
         if constexpr (HS != 0) {
           if (s_item[2]) {
-            batch_h_stage<K>(bp.pv[0], bp.Q, smem_raw);
+            if (var == 0) batch_h_stage<K, typename XSmem<float, K>::SV>(bp.pv[0], bp.Q, smem_raw);
+            else batch_h_stage<K, double>(bp.pv[0], bp.Q, smem_raw);
             __syncthreads();
             if (threadIdx.x == 0) {
               __threadfence();

@@ -4,6 +4,8 @@
 // CPU oracle has its own, separate implementation of the method.
 #pragma once
 
+#include <type_traits>
+
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

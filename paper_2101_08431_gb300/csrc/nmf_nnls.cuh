@@ -50,6 +50,41 @@ __device__ __forceinline__ double dot_masked(const double* a, const double (&b)[
   return t[0];
 }
 
+// Arithmetic of the lane-parallel solver in its value type: FP64 for the
+// FP64-class passes; FP32 for the FP32 pass, whose right-hand sides are
+// FP32-accurate (IEEE-ordered bit patterns for sign and order tests, the
+// correctly rounded FP32 reciprocal).
+template <typename V>
+struct VOps;
+template <>
+struct VOps<double> {
+  __device__ static long long bits(double x) { return __double_as_longlong(x); }
+  __device__ static double rcp(double x) { return rcp64(x); }
+  __device__ static double absv(double x) { return dabs(x); }
+};
+template <>
+struct VOps<float> {
+  __device__ static int bits(float x) { return __float_as_int(x); }
+  __device__ static float rcp(float x) { return __frcp_rn(x); }
+  __device__ static float absv(float x) { return fabsf(x); }
+};
+template <typename V>
+__device__ __forceinline__ bool vpos(V x) { return VOps<V>::bits(x) > 0; }   // x > 0
+template <typename V>
+__device__ __forceinline__ V vmax_nn(V a, V b) { return VOps<V>::bits(a) >= VOps<V>::bits(b) ? a : b; }
+
+template <int K, typename V>
+__device__ __forceinline__ V dot_masked_v(const V* a, const V (&b)[K], uint32_t P) {
+  V t[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) t[c] = ((P >> c) & 1u) ? a[c] * b[c] : V(0);
+#pragma unroll
+  for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+    for (int c = 0; c + w < K; c += 2 * w) t[c] += t[c + w];
+  return t[0];
+}
+
 template <int K>
 struct InvCache {
   int n;
@@ -475,13 +510,15 @@ struct LaneGroup {
     a = lane & (KP - 1);
     base = lane & ~(KP - 1);
   }
-  __device__ double from(double v, int c) const { return __shfl_sync(0xffffffffu, v, base + c); }
+  template <typename V>
+  __device__ V from(V v, int c) const { return __shfl_sync(0xffffffffu, v, base + c); }
   // the group's bits of a warp ballot, bit a of the result = lane base + a
   __device__ uint32_t bits(bool pred) const { return (__ballot_sync(0xffffffffu, pred) >> base) & GMASK; }
   // max over the group of non-negative values (integer order of the bits)
-  __device__ double max_nn(double v) const {
+  template <typename V>
+  __device__ V max_nn(V v) const {
 #pragma unroll
-    for (int o = 1; o < KP; o <<= 1) v = dmax_nn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 1; o < KP; o <<= 1) v = vmax_nn(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
   }
 };
@@ -496,9 +533,9 @@ struct LaneGroup {
 // behind the TMA stream of M).  Called by the `nthreads` threads starting at
 // thread t0 (both multiples of 32); sync() must be a barrier over exactly
 // those threads.  Warps without a subset in a round skip its arithmetic.
-template <int K, typename Sync>
-__device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, int* ok, int t0, int nthreads,
-                                         Sync sync) {
+template <int K, typename V, typename Sync>
+__device__ void build_subset_table_lanes_v(const V* Gm, V pivot_min, V* tab, int* ok, int t0, int nthreads,
+                                           Sync sync) {
   static_assert(K <= 8, "subset tables are built for k <= 8");
   constexpr int KP = LaneGroup<K>::KP, CPW = LaneGroup<K>::CPW;
   constexpr int NC = (1 << K) - 1;              // candidate subsets 1 .. 2^K - 1
@@ -536,25 +573,25 @@ __device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, in
       }
       const int h = 31 - __clz(P);
       const uint32_t par = P & ~(1u << h);
-      const double* A = tab + (size_t)par * K * K;
-      double gi[K];
+      const V* A = tab + (size_t)par * K * K;
+      V gi[K];
 #pragma unroll
-      for (int c = 0; c < K; ++c) gi[c] = S.G[c * K + h];
+      for (int c = 0; c < K; ++c) gi[c] = Gm[c * K + h];
       const bool ina = g.a < K && ((par >> g.a) & 1u);
-      const double u = ina ? dot_masked<K>(A + g.a * K, gi, par) : 0.0;
-      double t = ina ? S.G[h * K + g.a] * u : 0.0;
+      const V u = ina ? dot_masked_v<K, V>(A + g.a * K, gi, par) : V(0);
+      V t = ina ? Gm[h * K + g.a] * u : V(0);
 #pragma unroll
       for (int o = 1; o < KP; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      const double sp = S.G[h * K + h] - t;
-      const bool good = valid && (par == 0 || ok[par] != 0) && (sp > S.pivot_min);
-      const double rs = rcp64(sp);
-      const double ua = u * rs;
-      double* D = tab + (size_t)P * K * K + g.a * K;
+      const V sp = Gm[h * K + h] - t;
+      const bool good = valid && (par == 0 || ok[par] != 0) && (sp > pivot_min);
+      const V rs = VOps<V>::rcp(sp);
+      const V ua = u * rs;
+      V* D = tab + (size_t)P * K * K + g.a * K;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const double uc = g.from(u, c);
+        const V uc = g.from(u, c);
         if (valid && g.a < K) {
-          double v = 0.0;
+          V v = V(0);
           if (ina) {
             if ((par >> c) & 1u) v = fmad(ua, uc, A[g.a * K + c]);
             else if (c == h) v = -ua;
@@ -571,6 +608,13 @@ __device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, in
   }
 }
 
+// The FP64 table of NnlsSolver's G (the same arithmetic as its bordering).
+template <int K, typename Sync>
+__device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, int* ok, int t0, int nthreads,
+                                         Sync sync) {
+  build_subset_table_lanes_v<K, double>(S.G, S.pivot_min, tab, ok, t0, nthreads, sync);
+}
+
 // Solve the columns held by the warp.  Per lane: b = component a of the
 // right-hand side, y = component a of the warm start (in) / solution (out),
 // grow = row a of G (K values, registers).  tab / ok: subset table of G.
@@ -578,20 +622,20 @@ __device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, in
 // order; the per-column state machine acts through predicates only.
 // Returns per lane the column's status (0 converged, 1 iteration cap, -1 a
 // needed table entry is degenerate) and its passive set in *mask.
-template <int K>
-__device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const double* tab, const int* ok,
-                                               const double (&grow)[K], double gmax, double eps,
-                                               double b, double& y, bool warm, bool active,
-                                               bool refine, uint32_t* mask) {
+template <int K, typename V = double>
+__device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const V* tab, const int* ok,
+                                               const V (&grow)[K], V gmax, V eps, V b, V& y, bool warm,
+                                               bool active, bool refine, uint32_t* mask) {
+  using O = VOps<V>;
   constexpr int KP = LaneGroup<K>::KP;
   const bool comp = active && g.a < K;
-  double bc[K];
+  V bc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) bc[c] = g.from(b, c);
-  const double bmax = g.max_nn(comp ? dabs(b) : 0.0);
-  const bool ypos = comp && warm && dpos(y);
+  const V bmax = g.max_nn(comp ? O::absv(b) : V(0));
+  const bool ypos = comp && warm && vpos(y);
   uint32_t P = g.bits(ypos);
-  if (!ypos) y = 0.0;
+  if (!ypos) y = V(0);
   uint32_t blocked = 0;
   int t_in = -1, status = active ? 1 : 0;
   bool done = !active;
@@ -603,66 +647,66 @@ __device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const doub
     }
     if (__all_sync(0xffffffffu, done)) break;
     const bool inP = !done && ((P >> g.a) & 1u);
-    const double* A = tab + (size_t)(inP ? P : 0) * K * K + g.a * K;
-    double z0 = 0.0;
+    const V* A = tab + (size_t)(inP ? P : 0) * K * K + g.a * K;
+    V z0 = V(0);
     if (inP) {
 #pragma unroll
       for (int c = 0; c < K; ++c)
         if ((P >> c) & 1u) z0 = fmad(A[c], bc[c], z0);
     }
-    double r = b;   // r = b - G z0, all components
+    V r = b;   // r = b - G z0, all components
 #pragma unroll
     for (int c = 0; c < K; ++c) r = fmad(-grow[c], g.from(z0, c), r);
-    double z = z0;
+    V z = z0;
     if (refine) {   // one step of iterative refinement on P
-      const double rp = inP ? r : 0.0;
-      double corr = 0.0;
+      const V rp = inP ? r : V(0);
+      V corr = V(0);
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const double rc = g.from(rp, c);
+        const V rc = g.from(rp, c);
         if (inP && ((P >> c) & 1u)) corr = fmad(A[c], rc, corr);
       }
       z = z0 + corr;
     }
-    const uint32_t nonpos = g.bits(comp && inP && !dpos(z));
+    const uint32_t nonpos = g.bits(comp && inP && !vpos(z));
     // a just-entered variable that does not come out positive is blocked
     bool reject = false;
     if (t_in >= 0) reject = (nonpos >> t_in) & 1u;
     // Lawson-Hanson step (columns with nonpos != 0 and no rejection)
     const bool stepping = !done && !reject && nonpos;
-    double yn = 0.0;
+    V yn = V(0);
     uint32_t drop = 0;
     if (__any_sync(0xffffffffu, stepping)) {
       const bool mine = stepping && ((nonpos >> g.a) & 1u);
-      double ratio = 2.0;
+      V ratio = V(2);
       if (mine) {
-        ratio = y * rcp64(y - z);
-        if (!(dbits(ratio) >= 0)) ratio = 0.0;
+        ratio = y * O::rcp(y - z);
+        if (!(O::bits(ratio) >= 0)) ratio = V(0);
       }
-      double amin = ratio;
+      V amin = ratio;
 #pragma unroll
       for (int o = 1; o < KP; o <<= 1) {
-        const double w = __shfl_xor_sync(0xffffffffu, amin, o);
-        amin = dbits(w) < dbits(amin) ? w : amin;
+        const V w = __shfl_xor_sync(0xffffffffu, amin, o);
+        amin = O::bits(w) < O::bits(amin) ? w : amin;
       }
-      const uint32_t atmin = g.bits(mine && dbits(ratio) == dbits(amin));
-      const double alpha = atmin ? amin : 0.0;
-      yn = (stepping && inP) ? fmad(alpha, z - y, y) : 0.0;
+      const uint32_t atmin = g.bits(mine && O::bits(ratio) == O::bits(amin));
+      const V alpha = atmin ? amin : V(0);
+      yn = (stepping && inP) ? fmad(alpha, z - y, y) : V(0);
       const int q = stepping ? __ffs(atmin ? atmin : nonpos) - 1 : 0;
-      drop = g.bits(stepping && comp && inP && !dpos(yn));
+      drop = g.bits(stepping && comp && inP && !vpos(yn));
       if (stepping) drop |= 1u << q;
     }
     // entering test (feasible columns): w = b - G y, the residual of the solve
     const bool feas = !done && !reject && !nonpos;
-    const double yf = (feas && comp && inP) ? z : 0.0;
-    const double ymax = g.max_nn(yf);
-    const double tol = 10.0 * K * eps * (bmax + gmax * ymax);
-    const bool cand = feas && comp && !(((P | blocked) >> g.a) & 1u) && dgt_nn(r, tol);
+    const V yf = (feas && comp && inP) ? z : V(0);
+    const V ymax = g.max_nn(yf);
+    const V tol = V(10) * V(K) * eps * (bmax + gmax * ymax);
+    const bool cand = feas && comp && !(((P | blocked) >> g.a) & 1u) && O::bits(r) > O::bits(tol);
     const uint32_t cands = g.bits(cand);
-    double best = cand ? r : 0.0;
+    V best = cand ? r : V(0);
 #pragma unroll
-    for (int o = 1; o < KP; o <<= 1) best = dmax_nn(best, __shfl_xor_sync(0xffffffffu, best, o));
-    const uint32_t at = g.bits(cand && dbits(r) == dbits(best));
+    for (int o = 1; o < KP; o <<= 1) best = vmax_nn(best, __shfl_xor_sync(0xffffffffu, best, o));
+    const uint32_t at = g.bits(cand && O::bits(r) == O::bits(best));
     // apply the per-column transition
     if (!done) {
       if (reject) {
@@ -671,7 +715,7 @@ __device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const doub
         t_in = -1;
       } else if (nonpos) {
         t_in = -1;
-        y = ((drop >> g.a) & 1u) ? 0.0 : yn;
+        y = ((drop >> g.a) & 1u) ? V(0) : yn;
         P &= ~drop;
       } else {
         t_in = -1;
@@ -687,7 +731,7 @@ __device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const doub
       }
     }
   }
-  *mask = g.bits(comp && dpos(y));
+  *mask = g.bits(comp && vpos(y));
   return status;
 }
 

@@ -41,6 +41,13 @@ struct YTraits {
   static constexpr int VP = (V <= 1) ? 1 : (V <= 2) ? 2 : (V <= 4) ? 4 : (V <= 8) ? 8 : (V <= 16) ? 16 : 32;
   static_assert(V <= 32, "B tile must fit one warp reduce-scatter");
   static constexpr int ROWS = RPT * TC;                        // rows per CTA at most
+  // value type of the column solves: FP32 for the FP32 pass (its B is
+  // FP32-accurate), FP64 otherwise
+  static constexpr bool F32NN = !AR::XD && K <= 8;
+  using NV = typename std::conditional<F32NN, float, double>::type;
+  // the NNLS warp builds the table in shared memory: FP32 solves (k <= 8),
+  // FP64 solves at k <= 6 (k = 7, 8: the FP64 table built by the row pass)
+  static constexpr bool LOCAL_TAB = F32NN || K <= 6;
 };
 
 __host__ __device__ inline int wrap_col(int head, int j, int mcap) {
@@ -69,8 +76,11 @@ struct YSmem {
     double lt[32][NYT];                // per-lane KKT / objective terms (k <= 8)
     uint32_t samples[CACHE_N];
     InvCache<K> cache;                 // k > 8 only (no subset table)
-    double gtab[(K <= 6) ? (1 << K) * K * K : 1];   // subset table of G, staged (k <= 6)
-    int gok[(K <= 6) ? (1 << K) : 1];
+    // subset table of G built by the NNLS warp, in the value type of the
+    // solve: FP32 for the FP32 pass, FP64 otherwise; Gn: G in that type
+    typename Tr::NV gtab[Tr::LOCAL_TAB ? (1 << K) * K * K : 1];
+    int gok[Tr::LOCAL_TAB ? (1 << K) : 1];
+    typename Tr::NV Gn[K * K];
   };
   static constexpr size_t SMALL_BYTES = (sizeof(Small) + 127) & ~size_t(127);
   __host__ __device__ static constexpr size_t small_bytes() { return SMALL_BYTES; }
@@ -343,9 +353,18 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
       g.init();
       const int jj = lane / LaneGroup<K>::KP;
       const bool ca = g.a < K;
-      double grow[K];
+      using NV = typename Tr::NV;
+      constexpr bool F32NN = Tr::F32NN;
+      double grow[K];   // row a of G (FP64: the KKT terms)
 #pragma unroll
       for (int c = 0; c < K; ++c) grow[c] = ca ? sm.G[g.a * K + c] : 0.0;
+      if constexpr (F32NN) {
+        for (int e = lane; e < K * K; e += 32) sm.Gn[e] = (NV)sm.G[e];
+        __syncwarp();
+      }
+      NV grown[K];      // row a of G in the solve's type
+#pragma unroll
+      for (int c = 0; c < K; ++c) grown[c] = (NV)grow[c];
       double* acc_t = sm.lt[lane];
 #pragma unroll
       for (int e = 0; e < NYT; ++e) acc_t[e] = 0.0;
@@ -354,9 +373,17 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
       for (int c = 0; c < K; ++c) hacc[c] = 0.0;
       // k = 7, 8 always, k <= 6 when the row pass's tail has built it: the
       // table of G in global memory; otherwise this warp builds it below
-      const bool gglob = K > 6 || (p.tab_global && st->gtab_valid);
-      const double* gtab = gglob ? p.Gtab : sm.gtab;
-      const int* gok = gglob ? p.Gok : sm.gok;
+      // (FP32 solves: always this warp's own FP32 table)
+      const bool gglob = !F32NN && (K > 6 || (p.tab_global && st->gtab_valid));
+      const NV* gtab;
+      const int* gok;
+      if constexpr (F32NN) {
+        gtab = sm.gtab;
+        gok = sm.gok;
+      } else {
+        gtab = gglob ? p.Gtab : sm.gtab;
+        gok = gglob ? p.Gok : sm.gok;
+      }
       // warm start and passive set of the next tile, fetched one tile ahead
       double yo_nx = 0.0;
       uint32_t om_nx = 0;
@@ -366,9 +393,14 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         if (ca) yo_nx = p.Y[cur][(size_t)ph_nx * K + g.a];
         om_nx = p.ymask[cur][ph_nx];
       }
-      if constexpr (K <= 6) {
-        if (mode == MODE_SWEEP && !gglob)
-          build_subset_table_lanes<K>(solver, sm.gtab, sm.gok, NCW * 32, 32, [] { __syncwarp(); });
+      if constexpr (Tr::LOCAL_TAB) {
+        if (mode == MODE_SWEEP && !gglob) {
+          if constexpr (F32NN)
+            build_subset_table_lanes_v<K, NV>(sm.Gn, (NV)solver.pivot_min, sm.gtab, sm.gok, NCW * 32, 32,
+                                              [] { __syncwarp(); });
+          else
+            build_subset_table_lanes<K>(solver, sm.gtab, sm.gok, NCW * 32, 32, [] { __syncwarp(); });
+        }
       }
       for (int t = 0; t < ntiles; ++t) {
         const int slot = t & 1;
@@ -408,8 +440,10 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         double yn = yo;
         if (mode == MODE_SWEEP) {
           uint32_t msk = 0;
-          int stt = lane_table_nnls<K>(g, gtab, gok, grow, solver.gmax, AR::EPS, b, yn, p.warm != 0,
-                                       active, AR::XD, &msk);
+          NV ynv = (NV)yn;
+          int stt = lane_table_nnls<K, NV>(g, gtab, gok, grown, (NV)solver.gmax, (NV)AR::EPS, (NV)b, ynv,
+                                           p.warm != 0, active, AR::XD, &msk);
+          yn = (double)ynv;
           if (__any_sync(0xffffffffu, stt < 0)) {
             // a degenerate table entry: the group's first lane solves the
             // column with the incremental solver, then scatters the result
@@ -722,9 +756,14 @@ struct XSmem {
   }
   static constexpr int WT_NEED = (binom_mid() * LaneGroup<K>::KP + 31) / 32;
   static constexpr int WT = TABLE ? (WT_NEED < 1 ? 1 : (WT_NEED > Tr::NW / 2 ? Tr::NW / 2 : WT_NEED)) : 0;
+  // value type of the row solves: FP32 for the FP32 pass (P partials in
+  // FP32), FP64 otherwise
+  static constexpr bool F32NN = std::is_same<TA, float>::value && TABLE;
+  using SV = typename std::conditional<F32NN, float, double>::type;
   struct Small {
     double H[K * K];
     double Gs[K * K];
+    SV Hn[K * K];                      // H in the solve's type
     TA psum[Tr::NW][Tr::RB][K];
     double fin[Tr::NV];
     double yfin[NYT];
@@ -735,7 +774,7 @@ struct XSmem {
     unsigned ticket;
   };
   static constexpr size_t SMALL = (sizeof(Small) + 127) & ~size_t(127);
-  static constexpr size_t TAB = TABLE ? (size_t(1) << K) * K * K * sizeof(double) : 0;
+  static constexpr size_t TAB = TABLE ? (size_t(1) << K) * K * K * sizeof(SV) : 0;
   static constexpr size_t OK = TABLE ? (size_t(1) << K) * sizeof(int) : 0;
   __host__ __device__ static constexpr size_t bytes() { return SMALL + TAB + OK + 16; }
 };
@@ -761,8 +800,10 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   constexpr bool TABLE = Xs::TABLE;
   typename Xs::Small& xs = *reinterpret_cast<typename Xs::Small*>(xsm_raw);
   // tab_global: H and its subset table come from the batch's H stage
+  using SV = typename Xs::SV;   // value type of the row solves
+  constexpr bool F32NN = Xs::F32NN;
   const bool hglob = TABLE && p.tab_global && mode == MODE_SWEEP;
-  double* tab = hglob ? p.Htab : reinterpret_cast<double*>(xsm_raw + Xs::SMALL);
+  SV* tab = hglob ? reinterpret_cast<SV*>(p.Htab) : reinterpret_cast<SV*>(xsm_raw + Xs::SMALL);
   int* tok = hglob ? p.Hok : reinterpret_cast<int*>(xsm_raw + Xs::SMALL + Xs::TAB);
   double* H = xs.H;
   double* Gs = xs.Gs;
@@ -803,7 +844,14 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     if constexpr (TABLE) {
       NnlsSolver<K> ts;
       ts.init(H, 2.220446049250313e-16);
-      build_subset_table_lanes<K>(ts, tab, tok, 0, wt * 32, [wt] { named_sync(2, wt * 32); });
+      if constexpr (F32NN) {
+        for (int e = tid; e < K * K; e += wt * 32) xs.Hn[e] = (SV)H[e];
+        named_sync(2, wt * 32);
+        build_subset_table_lanes_v<K, SV>(xs.Hn, (SV)ts.pivot_min, tab, tok, 0, wt * 32,
+                                          [wt] { named_sync(2, wt * 32); });
+      } else {
+        build_subset_table_lanes<K>(ts, tab, tok, 0, wt * 32, [wt] { named_sync(2, wt * 32); });
+      }
     }
   } else {
     using PO = PartOps<TA>;
@@ -836,7 +884,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     if (mode == MODE_SWEEP) build_cache<K>(&cache, solver, samples, CACHE_N);
   }
 
-  if (TABLE) {
+  if constexpr (TABLE) {
     // lanes <-> (row slot jj, component a): warps 0 .. NWN-1 hold the 32 rows
     constexpr int KP = LaneGroup<K>::KP, CPW = LaneGroup<K>::CPW, NWN = RB / CPW;
     auto& gram_w = xs.gram_w;
@@ -851,6 +899,9 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       double hrow[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) hrow[c] = ca ? H[g.a * K + c] : 0.0;
+      SV hrown[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) hrown[c] = (SV)hrow[c];
       double pr = 0.0, xo = 0.0;
       uint32_t old_mask = 0;
       if (comp) {
@@ -864,8 +915,11 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       uint32_t msk = 0;
       int stt = 0;
       if (mode == MODE_SWEEP) {
-        stt = lane_table_nnls<K>(g, tab, tok, hrow, solver.gmax, 2.220446049250313e-16, pr, xn,
-                                 p.warm != 0, ract, true, &msk);
+        SV xnv = (SV)xn;
+        stt = lane_table_nnls<K, SV>(g, tab, tok, hrown, (SV)solver.gmax,
+                                     F32NN ? (SV)1.1920928955078125e-07 : (SV)2.220446049250313e-16, (SV)pr,
+                                     xnv, p.warm != 0, ract, true, &msk);
+        xn = (double)xnv;
         if (__any_sync(0xffffffffu, stt < 0)) {
           double bb[K], xx[K];
 #pragma unroll
@@ -967,7 +1021,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       p.Xpart[(size_t)blk * NV + e] = r;
     }
     __threadfence();
-  } else if (warp == 0) {
+  } else if (warp == 0) {   // k = 16
     double v[Tr::NVC * 32];
 #pragma unroll
     for (int e = 0; e < Tr::NVC * 32; ++e) v[e] = 0.0;
@@ -985,7 +1039,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       int stt = 0;
       if (mode == MODE_SWEEP) {
         stt = -1;
-        if (TABLE) stt = table_nnls<K>(solver, tab, tok, pr, xn, p.warm != 0, &msk);
+        // k = 16 (no table): the incremental solver
         if (stt < 0) {
           double Ascr[K * K];
 #pragma unroll

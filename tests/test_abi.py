@@ -92,3 +92,9 @@ def test_server_arguments_rejected_before_any_device_work(lib):
 def test_library_is_built_for_sm_103a_only():
     from paper_2101_08431_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_selftest_rejects_bad_limit(lib):
+    from paper_2101_08431_gb300 import _native
+    assert lib.nmf_selftest_bounded_wait(0, None) == _native.NMF_EINVAL
+    assert lib.nmf_selftest_bounded_wait(1 << 30, None) == _native.NMF_EINVAL

@@ -186,3 +186,20 @@ def test_batch_rejects_bad_input():
             b.sweep(1)
         with pytest.raises(NMFError):
             b.set_pass_mode(1)          # the FP64-accumulated pass is not a batch mode
+
+
+def test_bounded_wait_reports_timeout():
+    """The dependency wait of the batched form gives up after its poll limit
+    on a counter nothing increments, and reports NMF_ETIMEOUT through the
+    control block; the context stays usable."""
+    _lib()
+    import time
+    import torch
+    from paper_2101_08431_gb300 import _native
+    L = _native.load()
+    t0 = time.time()
+    assert L.nmf_selftest_bounded_wait(20000, None) == _native.NMF_ETIMEOUT
+    assert time.time() - t0 < 30.0
+    assert L.nmf_selftest_bounded_wait(0, None) == _native.NMF_EINVAL
+    x = torch.ones(16, device="cuda")
+    assert float(x.sum().item()) == 16.0        # the device still answers
