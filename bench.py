@@ -316,6 +316,9 @@ def run_ours(args):
                   "step": "append all m columns from pinned host memory, one sweep, read the statistics"}
     hm.close()
     hf.close()
+    # ---- mixed precision at scale: rank 16 on the tensor cores
+    if not args.skip_k16:
+        out["rank16"] = rank16_leg(args, sptr, barrier)
     # ---- batched persistent form: 256 uneven problems
     if not args.skip_batch:
         out["batched"] = batched_leg(args, rank, sptr, barrier, max_over_ranks, world)
@@ -341,11 +344,70 @@ def run_ours(args):
                        "state": "steady state: timed sweeps follow %d sweeps from the U[0,1] start" % PRECOND,
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU"}}
     for key in ("roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks", "refine_pass", "fp64_form",
-                "time_to_kkt", "batched", "serving"):
+                "time_to_kkt", "rank16", "batched", "serving"):
         if key in out:
             line[key] = out[key]
     print(json.dumps(line), flush=True)
     return 0
+
+
+K16_N, K16_M, K16_K, K16_NOISE, K16_PRECOND = 8192, 16384, 16, 1e-4, 30
+
+
+def rank16_leg(args, sptr, barrier):
+    """Mixed precision at scale: n=8192, m=16384, k=16, FP32 M (512 MB, > L2,
+    so no flush between timed sweeps), the FP32-class pass on the tensor
+    cores (split-BF16 contractions, FP64 solves).  Timed after K16_PRECOND
+    sweeps from the U[0,1] start.  Reports sweeps/s, the M pass's HBM GB/s
+    against the measured peak and its issued MMA TFLOP/s.  (The error of this
+    pass against the FP64 oracle, on sampled columns and rows of the same
+    workload, is checked by the test suite.)"""
+    import torch
+    import synth
+    from paper_2101_08431_gb300 import NMF_PREC_MIXED, StreamingNMF
+    n, m, k = K16_N, K16_M, K16_K
+    M, _, _ = synth.pdf_like(n, m, k, noise=K16_NOISE, relative=True, seed=11)
+    M32 = np.asfortranarray(M.astype(np.float32))
+    del M
+    X0, Y0 = synth.init_factors(n, m, k, seed=11)
+    stream = torch.cuda.current_stream()
+    h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=0.0, stream=sptr)
+    h.append_columns(M32)
+    h.set_factors(X0, Y0)
+    h.set_pass_mode(0)
+    h.sweep(K16_PRECOND, want_stats=False)
+    steps = max(10, args.steps // 10)
+    for _ in range(3):
+        h.sweep(1, want_stats=False)
+    h.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    for e0, e1 in ev:
+        e0.record(stream)
+        h.sweep(1, want_stats=False)
+        e1.record(stream)
+    barrier()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    tm = h.get_timing()
+    h.set_timing(False)
+    y_ms = tm["ypass_ms"] / max(tm["ypass_launches"], 1)
+    x_ms = tm["xpass_ms"] / max(tm["xpass_launches"], 1)
+    alg = n * m * 4 + 2 * m * k * 8 + n * k * 8
+    mma_flops = n * m * 384.0      # issued: B-MMA 64x32x16 per 16 rows x 16 columns, P-MMA 4 x 128x16x16
+    peak, peak_kind = peaks()
+    kk = h.objective_kkt()
+    h.close()
+    return {"workload": "PDF-like n=8192 m=16384 k=16 (1e-4 rel. noise), FP32 M (512 MB), tensor-core "
+                        "FP32-class pass (split-BF16 tcgen05 contractions, FP64 solves)",
+            "state": "timed sweeps follow %d sweeps from the U[0,1] start" % K16_PRECOND,
+            "l2": "inputs larger than L2 (no flush)",
+            "sweeps_per_s": steps / (ms / 1e3), "ms_per_sweep": ms / steps,
+            "ypass_avg_ms": y_ms, "xpass_avg_ms": x_ms,
+            "ypass_hbm_gbs": alg / (y_ms / 1e3) / 1e9, "ypass_hbm_frac": alg / (y_ms / 1e3) / 1e9 / peak,
+            "peak_gbs": peak, "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
+            "ypass_mma_tflops_issued": mma_flops / (y_ms / 1e3) / 1e12,
+            "columns_per_s": m * steps / (ms / 1e3),
+            "kkt_rel_after": kk["kkt_rel"], "f_after": kk["f"]}
 
 
 BATCH_NPROB = 256
@@ -517,6 +579,20 @@ def run_ncu_case(args):
         b.close()
         print("ncu case batch: 16 problems, 3 sweeps")
         return 0
+    if args.ncu_case == "k16":
+        import synth
+        n, m, k = K16_N, 6144, K16_K     # 192 MB of FP32 M: above L2, a small device footprint
+        M, _, _ = synth.pdf_like(n, m, k, noise=K16_NOISE, relative=True, seed=11)
+        X, Y = synth.init_factors(n, m, k, seed=11)
+        h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=0.0)
+        h.append_columns(np.asfortranarray(M, dtype=np.float32))
+        h.set_factors(X, Y)
+        h.set_pass_mode(0)
+        h.sweep(args.ncu_precond + 3, want_stats=False)
+        torch.cuda.synchronize()
+        h.close()
+        print("ncu case k16: n=%d m=%d, 1 priming pair + %d sweeps" % (n, m, args.ncu_precond + 3))
+        return 0
     M32, M64, X0, Y0 = make_data(0)
     fp64 = args.ncu_case == "f64"
     h = StreamingNMF(N_ROWS, RANK_K, M_COLS, prec=NMF_PREC_FP64 if fp64 else NMF_PREC_MIXED, kkt_target=0.0)
@@ -541,10 +617,11 @@ def main():
     ap.add_argument("--skip-ttk", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-problem batched leg")
     ap.add_argument("--skip-serve", action="store_true", help="skip the streaming-serving leg")
+    ap.add_argument("--skip-k16", action="store_true", help="skip the rank-16 tensor-core leg")
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--batch-ttk", action="store_true",
                     help="also run every batched problem to relative KKT 1e-8")
-    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "batch"], default=None,
+    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "batch", "k16"], default=None,
                     help="run only a short launch sequence for an ncu capture")
     ap.add_argument("--ncu-precond", type=int, default=200)
     args = ap.parse_args()

@@ -8,6 +8,7 @@
 
 #include "nmf.h"
 #include "nmf_internal.h"
+#include "nmf_tc16.h"
 
 using namespace nmfgb;
 
@@ -187,6 +188,11 @@ struct nmf_handle {
     int seen_m = -1, seen_head = -1;   // last signature run uncaptured
   };
   ChunkGraph graphs[NVAR];
+  // rank 16, mixed precision: the FP32-class pass runs on the tensor cores
+  bool tc16 = false;
+  Tc16Plan tc16_L{};              // plan of the last launch, for tc16_m resident columns
+  int tc16_m = -1;
+  bool refine_ok = true;          // the FP64-class M passes have a plan for n
   // per-kernel timing (event triplets around each sweep's two launches)
   bool timing = false;
   static constexpr int NEV = 512;
@@ -305,8 +311,20 @@ nmf_status drain_timing(nmf_handle* h) {
 
 // One sweep (M pass + row pass) or, with mode PRIME, the priming pair.
 nmf_status launch_pair(nmf_handle* h, int var, int mode) {
-  YPlan L;
-  if (!make_plan(h, var, &L)) return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  YPlan L{};
+  Tc16Plan T{};
+  const bool use_tc = h->tc16 && var == VAR_F32;
+  if (use_tc) {
+    if (h->tc16_m != h->m) {
+      if (!tc16_plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
+        return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
+      h->tc16_m = h->m;
+    }
+    T = h->tc16_L;
+    L.Q = T.Q;
+  } else if (!make_plan(h, var, &L)) {
+    return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  }
   Problem p = make_problem(h, var);
   const bool timed = h->timing && mode == MODE_SWEEP;
   if (timed && h->nev == nmf_handle::NEV) {
@@ -318,7 +336,8 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode) {
       for (int j = 0; j < 3; ++j) CUDA_TRY(h, cudaEventCreate(&h->ev[h->nev][j]));
     CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][0], h->stream));
   }
-  CUDA_TRY(h, h->ks[var].ypass(p, mode, L, h->stream));
+  if (use_tc) CUDA_TRY(h, tc16_launch(p, mode, T, h->stream));
+  else CUDA_TRY(h, h->ks[var].ypass(p, mode, L, h->stream));
   if (timed) CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][1], h->stream));
   CUDA_TRY(h, h->ks[var].xpass(p, mode, L.Q, h->nxblk, h->stream));
   if (timed) {
@@ -377,6 +396,7 @@ nmf_status launch_chunk(nmf_handle* h, int var, int chunk) {
 
 int variant_for(const nmf_handle* h) {
   if (!h->store_f32) return VAR_F64;
+  if (!h->refine_ok) return VAR_F32;
   if (h->forced_mode == 0) return VAR_F32;
   if (h->forced_mode == 1) return VAR_REF;
   if (h->forced_mode == 2) return VAR_DF;
@@ -511,15 +531,24 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
       for (int ci = 0; ci < 4; ++ci)
         h->max_clusters[v][ci] = h->ks[v].max_clusters(1 << ci, (size_t)h->smem_optin);
   {
-    // every variant this handle may run must have a plan for n
+    // every variant this handle may run must have a plan for n; at rank 16
+    // with FP32 M the FP32-class pass is the tensor-core pass, and a handle
+    // whose n is beyond the FP64-class kernels runs that pass alone
+    Tc16Plan T{};
+    h->tc16 = h->store_f32 && k == 16 && tc16_plan(h->ld, h->mcap, h->nsm, h->smem_optin, &T);
     const int need[3] = {h->store_f32 ? VAR_F32 : VAR_F64, h->store_f32 ? VAR_REF : VAR_F64,
                          h->store_f32 ? VAR_DF : VAR_F64};
     for (int v : need) {
+      if (v == VAR_F32 && h->tc16) continue;
       YPlan L;
       int msave = h->m;
       h->m = h->mcap;
       const bool ok = h->has[v] && make_plan(h, v, &L);
       h->m = msave;
+      if (!ok && h->tc16 && v != VAR_F32) {
+        h->refine_ok = false;
+        continue;
+      }
       if (!ok) return bail(NMF_EINVAL, "n too large for the kernels of this precision");
     }
   }
@@ -682,7 +711,7 @@ nmf_status nmf_set_factors(nmf_handle* h, const double* X, const double* Y, int3
   h->phase = 0;
   h->best_rel = -1.0;
   h->chunks_since_best = 0;
-  nmf_status s = launch_pair(h, h->store_f32 ? VAR_REF : VAR_F64, MODE_PRIME);
+  nmf_status s = launch_pair(h, h->store_f32 ? (h->refine_ok ? VAR_REF : VAR_F32) : VAR_F64, MODE_PRIME);
   if (s != NMF_OK) return s;
   s = read_state(h);
   if (s != NMF_OK) return s;
@@ -814,12 +843,27 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
   if (!h) return NMF_EINVAL;
   if (h->poisoned) return h->poisoned;
   if (!h->factors_set) return fail(h, NMF_ESTATE, "factors not set");
-  const int var = h->store_f32 ? VAR_REF : VAR_F64;
-  YPlan L;
-  if (!make_plan(h, var, &L)) return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  // the FP64-contraction pass where it has a plan, else (rank 16 beyond its
+  // rows) the tensor-core pass
+  const int var = h->store_f32 ? (h->refine_ok ? VAR_REF : VAR_F32) : VAR_F64;
+  YPlan L{};
+  Tc16Plan T{};
+  const bool use_tc = h->tc16 && var == VAR_F32;
+  if (use_tc) {
+    if (h->tc16_m != h->m) {
+      if (!tc16_plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
+        return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
+      h->tc16_m = h->m;
+    }
+    T = h->tc16_L;
+    L.Q = T.Q;
+  } else if (!make_plan(h, var, &L)) {
+    return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  }
   Problem p = make_problem(h, var);
   CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
-  CUDA_TRY(h, h->ks[var].ypass(p, MODE_KKT, L, h->stream));
+  if (use_tc) CUDA_TRY(h, tc16_launch(p, MODE_KKT, T, h->stream));
+  else CUDA_TRY(h, h->ks[var].ypass(p, MODE_KKT, L, h->stream));
   kkt_stats_kernel<<<1, 32, 0, h->stream>>>(p, L.Q, h->dKkt);
   h->launches += 2;
   CUDA_TRY(h, cudaGetLastError());

@@ -1,0 +1,186 @@
+"""GPU parity of the rank-16 tensor-core M pass (split-BF16 tcgen05
+contractions, FP64 column solves), through the C ABI.
+
+The FP32-class pass of the mixed form at k = 16 runs B = X^T M and P = M Y^T
+as (M_hi + M_lo)(V_hi + V_lo) BF16 products with FP32 accumulation.  Each of
+hi, lo carries 8 significant bits, so the pair represents a value to within
+2^-18 of its magnitude; the products and the FP32 sums of a contraction of
+length L then carry a relative error of about 2 * 2^-18 + L^(1/2) 2^-24
+(< 1e-5 for the sizes here).  A half-sweep amplifies the error of its
+right-hand side by the condition number of its Gram (G = X^T X for Y,
+H = Y Y^T for X), so the bar of one sweep is max(5e-4, 3e-5 cond).
+
+Shapes cover a single CTA per column range (C = 1), clusters of 2, 4 and 16
+CTAs (rows split), CTAs that own no rows, a ragged last tile of columns and
+several tiles per cluster.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_08431_gb300 import StreamingNMF, build
+    build.build()
+    return StreamingNMF
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _warm_state(n, m, seed, sweeps):
+    M, _, _ = synth.pdf_like(n, m, 16, noise=1e-3, relative=True, seed=seed)
+    M32 = np.asfortranarray(M.astype(np.float32))
+    M64 = M32.astype(np.float64)
+    X, Y = synth.init_factors(n, m, 16, seed=seed)
+    if sweeps:
+        X, Y, _, _, _, _, st = oracle.anls(M64, X, Y, max_sweeps=sweeps)
+        assert st == oracle.OK
+    return M32, M64, np.ascontiguousarray(X), np.ascontiguousarray(Y)
+
+
+# (n, m, seed): C = 1 (200 rows); C = 2 (700, 1000); C = 4 (2048); C = 16 with
+# empty CTAs (4100); ragged last tiles (m = 150, 33, 300 not multiples of 16)
+SHAPES = [(200, 50, 1), (700, 150, 2), (1000, 64, 3), (2048, 300, 4), (4100, 33, 5)]
+
+
+@pytest.mark.parametrize("n,m,seed", SHAPES)
+def test_tc16_one_sweep_parity(n, m, seed):
+    S = _lib()
+    M32, M64, X, Y = _warm_state(n, m, seed, sweeps=12)
+    Xo, Yo, xmo, ymo, st = oracle.sweep(M64, X, Y)
+    assert st == oracle.OK
+    h = S(n, 16, m, prec=1, kkt_target=0.0)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    h.set_pass_mode(0)
+    h.sweep(1)
+    Xg, Yg, xmg, ymg = h.get_factors()
+    h.close()
+    bar_y = max(5e-4, 3e-5 * np.linalg.cond(X.T @ X))
+    bar_x = max(5e-4, 3e-5 * np.linalg.cond(Yo @ Yo.T))
+    ey, ex = _rel(Yg, Yo), _rel(Xg, Xo)
+    print("tc16 n=%d m=%d: rel err Y %.2e (bar %.1e), X %.2e (bar %.1e)" % (n, m, ey, bar_y, ex, bar_x))
+    assert ey <= bar_y, (ey, bar_y)
+    assert ex <= bar_x, (ex, bar_x)
+    # passive sets: where they differ, the component is one the pass's
+    # perturbation of B (or P) can move across zero, i.e. its value in both
+    # solutions is within the error bar of the half-sweep
+    _check_masks(Yg, Yo, ymg, ymo, bar_y, axis=0)
+    _check_masks(Xg, Xo, xmg, xmo, bar_x, axis=1)
+
+
+def _check_masks(Vg, Vo, mg, mo, bar, axis):
+    """Vg, Vo: k x m (axis 0: bits run down a column) or n x k (axis 1)."""
+    k = Vo.shape[axis]
+    bits = (1 << np.arange(k, dtype=np.uint64)).astype(np.uint64)
+    if axis == 0:
+        pg = (mg[None, :].astype(np.uint64) & bits[:, None]) != 0
+        po = (mo[None, :].astype(np.uint64) & bits[:, None]) != 0
+    else:
+        pg = (mg[:, None].astype(np.uint64) & bits[None, :]) != 0
+        po = (mo[:, None].astype(np.uint64) & bits[None, :]) != 0
+    diff = pg != po
+    scale = np.abs(Vo).max()
+    worst = np.maximum(np.abs(Vg), np.abs(Vo))[diff].max() if diff.any() else 0.0
+    print("  mask differences %d of %d entries, largest value there %.2e (bar x max %.2e)"
+          % (diff.sum(), diff.size, worst, bar * scale))
+    assert worst <= bar * scale
+
+
+def test_tc16_cold_start_sweeps_decrease_objective():
+    """From the U[0,1] start, tensor-core sweeps decrease the objective the
+    oracle computes for each iterate (Sec. 2: every ANLS half-step is a
+    minimisation, up to the pass's rounding)."""
+    S = _lib()
+    n, m = 1000, 96
+    M32, M64, X, Y = _warm_state(n, m, 9, sweeps=0)
+    h = S(n, 16, m, prec=1, kkt_target=0.0)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    h.set_pass_mode(0)
+    f_prev = oracle.objective(M64, X, Y)
+    for _ in range(6):
+        h.sweep(1)
+        Xg, Yg, _, _ = h.get_factors()
+        f = oracle.objective(M64, Xg, Yg)
+        assert f <= f_prev * (1 + 1e-5), (f, f_prev)
+        f_prev = f
+    h.close()
+
+
+def test_tc16_well_conditioned_tight_bar():
+    """Components with nearly disjoint supports: cond(G) is small, so the bar
+    is the pass's own error, 5e-4 (split-BF16 products are good to ~1e-5)."""
+    S = _lib()
+    n, m, k = 3000, 500, 16
+    g = np.random.default_rng(41)
+    r = np.arange(n, dtype=np.float64)
+    X0 = np.stack([np.exp(-0.5 * ((r - (c + 0.5) * n / k) / (n / (8.0 * k))) ** 2) for c in range(k)], axis=1)
+    Y0 = g.uniform(0.1, 1.0, size=(k, m))
+    M = X0 @ Y0
+    M += g.normal(0.0, 1e-3 * np.sqrt(np.mean(M ** 2)), size=M.shape)
+    M32 = np.asfortranarray(M.astype(np.float32))
+    M64 = M32.astype(np.float64)
+    X, Y = synth.init_factors(n, m, k, seed=41)
+    X, Y, _, _, _, _, st = oracle.anls(M64, X, Y, max_sweeps=8)
+    assert st == oracle.OK
+    X, Y = np.ascontiguousarray(X), np.ascontiguousarray(Y)
+    Xo, Yo, xmo, ymo, st = oracle.sweep(M64, X, Y)
+    h = S(n, k, m, prec=1, kkt_target=0.0)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    h.set_pass_mode(0)
+    h.sweep(1)
+    Xg, Yg, xmg, ymg = h.get_factors()
+    h.close()
+    cy, cx = np.linalg.cond(X.T @ X), np.linalg.cond(Yo @ Yo.T)
+    bar_y, bar_x = max(5e-4, 3e-5 * cy), max(5e-4, 3e-5 * cx)
+    ey, ex = _rel(Yg, Yo), _rel(Xg, Xo)
+    print("well-conditioned: cond G %.1f, H %.1f; rel err Y %.2e X %.2e" % (cy, cx, ey, ex))
+    assert ey <= bar_y and ex <= bar_x, (ey, bar_y, ex, bar_x)
+
+
+def test_tc16_full_size_sampled():
+    """The 8192 x 16384 x 16 workload (512 MB of FP32 M) in the launch
+    configuration the benchmark times: one tensor-core sweep from the U[0,1]
+    start, checked on 512 sampled columns (the oracle's column solve with the
+    input X) and 1024 sampled rows (the oracle's row solve with the sweep's
+    own new Y, so that every sampled row is an exact one-row problem)."""
+    S = _lib()
+    n, m, k = 8192, 16384, 16
+    M, _, _ = synth.pdf_like(n, m, k, noise=1e-4, relative=True, seed=3)
+    M32 = np.asfortranarray(M.astype(np.float32))
+    del M
+    X, Y = synth.init_factors(n, m, k, seed=3)
+    h = S(n, k, m, prec=1, kkt_target=0.0)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    h.set_pass_mode(0)
+    h.sweep(1)
+    Xg, Yg, _, _ = h.get_factors()
+    kk = h.objective_kkt()
+    h.close()
+    g = np.random.default_rng(5)
+    J = np.sort(g.choice(m, size=512, replace=False))
+    I = np.sort(g.choice(n, size=1024, replace=False))
+    G = X.T @ X
+    Yref = np.stack([oracle.nnls(G, X.T @ M32[:, j].astype(np.float64))[0] for j in J], axis=1)
+    H = Yg @ Yg.T
+    Xref = np.stack([oracle.nnls(H, Yg @ M32[i, :].astype(np.float64))[0] for i in I], axis=0)
+    bar_y = max(5e-4, 3e-5 * np.linalg.cond(G))
+    bar_x = max(5e-4, 3e-5 * np.linalg.cond(H))
+    ey, ex = _rel(Yg[:, J], Yref), _rel(Xg[I, :], Xref)
+    f_or = oracle.objective(M32.astype(np.float64), Xg, Yg)
+    print("full size: rel err Y %.2e (bar %.1e) X %.2e (bar %.1e); f %.6e vs oracle %.6e"
+          % (ey, bar_y, ex, bar_x, kk["f"], f_or))
+    assert ey <= bar_y and ex <= bar_x, (ey, bar_y, ex, bar_x)
+    assert abs(kk["f"] - f_or) <= 1e-3 * abs(f_or)
