@@ -1,0 +1,297 @@
+// Lawson-Hanson NNLS of 16-variable problems on 16-lane groups (lane a <->
+// variable a): the column solves of the rank-16 tensor-core M pass and the
+// row solves of the rank-16 row pass.
+#pragma once
+
+#include "nmf_common.cuh"
+#include "nmf_nnls.cuh"
+
+namespace nmfgb {
+
+// ---------------------------------------------------------------------------
+// One 16-variable problem on a 16-lane group (lane a <-> variable a), the same algorithm and decisions as the one-thread solver:
+// warm start from the support of y, entering test w_a > tol with
+// tol = 10 k eps (max|b| + max G_aa max|y|), lowest index on ties, Schur
+// pivot <= 1e-14 max G_aa blocks the variable, at most 5k + 10 outer steps.
+// A = inv(G_PP) is kept row-distributed (lane a holds row a) and carried from
+// column to column: a column whose warm passive set equals the carried one
+// costs two lane-parallel mat-vecs.  V is the value type of the solve.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double vrcp(double x) { return rcp64(x); }
+
+template <typename V>
+struct LaneNnls16 {
+  static constexpr int K = 16;
+  static constexpr int UPD_MAX = 48;   // rank-one updates of a carried inverse before it is rebuilt
+  const V (*Gp)[K + 1];
+  V A[K];             // row a of inv(G_PcPc)
+  uint32_t Pc;        // passive set of the carried inverse
+  int upd;            // rank-one updates since it was built
+  V gmax, pivot_min, eps;
+  int a, base;
+  unsigned gm;
+
+  __device__ void init(const V (*G)[K + 1], V eps_) {
+    Gp = G;
+    const int lane = threadIdx.x & 31;
+    a = lane & 15;
+    base = lane & 16;
+    gm = 0xFFFFu << base;
+    V g = 0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) g = fmax(g, fabs(G[c][c]));
+    gmax = g;
+    pivot_min = (V)1e-14 * g;
+    eps = eps_;
+#pragma unroll
+    for (int c = 0; c < K; ++c) A[c] = 0;
+    Pc = 0;
+    upd = 0;
+  }
+  __device__ __forceinline__ V bc(V v, int c) const { return __shfl_sync(gm, v, base + c); }
+  __device__ __forceinline__ V gsum(V v) const {
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(gm, v, o);
+    return v;
+  }
+  __device__ __forceinline__ V gmaxv(V v) const {
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v = fmax(v, __shfl_xor_sync(gm, v, o));
+    return v;
+  }
+  __device__ __forceinline__ uint32_t gballot(bool p) const { return (__ballot_sync(gm, p) >> base) & 0xFFFFu; }
+  __device__ __forceinline__ bool in(uint32_t P) const { return (P >> a) & 1u; }
+
+  // z_P = A b_P (zero outside P)
+  __device__ V apply(uint32_t P, V b) const {
+    V z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const V v = ((P >> c) & 1u) ? bc(b, c) : (V)0;
+      if ((c & 3) == 0) z0 = fmad(A[c], v, z0);
+      else if ((c & 3) == 1) z1 = fmad(A[c], v, z1);
+      else if ((c & 3) == 2) z2 = fmad(A[c], v, z2);
+      else z3 = fmad(A[c], v, z3);
+    }
+    return in(P) ? (z0 + z1) + (z2 + z3) : (V)0;
+  }
+  // (G y)_a
+  __device__ V gdot(V y) const {
+    V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const V v = bc(y, c);
+      if ((c & 3) == 0) s0 = fmad(Gp[a][c], v, s0);
+      else if ((c & 3) == 1) s1 = fmad(Gp[a][c], v, s1);
+      else if ((c & 3) == 2) s2 = fmad(Gp[a][c], v, s2);
+      else s3 = fmad(Gp[a][c], v, s3);
+    }
+    return (s0 + s1) + (s2 + s3);
+  }
+  // entering variable of the outer loop (or -1)
+  __device__ int entering(V b, V y, uint32_t P, uint32_t blocked, V bmax) const {
+    const V ymax = gmaxv(y);
+    const V tol = (V)(10.0 * K) * eps * (bmax + gmax * ymax);
+    const V w = b - gdot(y);
+    const bool cand = !(((P | blocked) >> a) & 1u) && w > tol;
+    V bw = cand ? w : (V)-1;
+    int bi = cand ? a : 99;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+      const V ow = __shfl_xor_sync(gm, bw, o);
+      const int oi = __shfl_xor_sync(gm, bi, o);
+      if (ow > bw || (ow == bw && oi < bi)) {
+        bw = ow;
+        bi = oi;
+      }
+    }
+    return bi < K ? bi : -1;
+  }
+  // A = inv(G_PP) -> inv(G_{P+i}); false (A unchanged) if the pivot fails
+  __device__ bool add(uint32_t P, int i) {
+    V u0 = 0, u1 = 0, gia = 0, gii = 0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const V g = __shfl_sync(gm, Gp[a][c], base + i);   // G[i][c] = G[c][i]
+      if (c == a) gia = g;
+      if (c == i) gii = g;
+      const V v = ((P >> c) & 1u) ? g : (V)0;
+      if (c & 1) u1 = fmad(A[c], v, u1);
+      else u0 = fmad(A[c], v, u0);
+    }
+    const V u = in(P) ? u0 + u1 : (V)0;
+    const V s = gii - gsum(gia * u);
+    if (!(s > pivot_min)) return false;
+    const V rs = vrcp(s);
+    const V ua = u * rs;
+    const bool pa = in(P);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const V uc = bc(u, c);
+      const bool pc = (P >> c) & 1u;
+      if (a == i) A[c] = pc ? -uc * rs : (c == i ? rs : (V)0);
+      else if (pa) {
+        if (pc) A[c] = fmad(ua, uc, A[c]);
+        else if (c == i) A[c] = -ua;
+      }
+    }
+    ++upd;
+    return true;
+  }
+  // A = inv(G_PP), i in P -> inv(G_{P-i})
+  __device__ void remove(uint32_t P, int i) {
+    V cia = 0;
+#pragma unroll
+    for (int c = 0; c < K; ++c)
+      if (c == i) cia = A[c];
+    const V rd = vrcp(bc(cia, i));
+    const V f = cia * rd;
+    const bool keep = in(P) && a != i;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const V cc = bc(cia, c);
+      if (keep && ((P >> c) & 1u) && c != i) A[c] = fmad(-f, cc, A[c]);
+    }
+    ++upd;
+  }
+  // carried inverse -> inverse for P (variables whose pivot fails are blocked)
+  __device__ uint32_t rebase(uint32_t P, uint32_t& blocked) {
+    const uint32_t diff = Pc ^ P;
+    if (Pc == 0 || upd > UPD_MAX || __popc(diff) > __popc(P)) {
+      uint32_t Q = 0, rest = P;
+      upd = 0;
+      while (rest) {
+        const int i = __ffs(rest) - 1;
+        rest &= rest - 1;
+        if (add(Q, i)) Q |= 1u << i;
+        else blocked |= 1u << i;
+      }
+      Pc = Q;
+      return Q;
+    }
+    uint32_t out = Pc & ~P;
+    while (out) {
+      const int i = __ffs(out) - 1;
+      out &= out - 1;
+      remove(Pc, i);
+      Pc &= ~(1u << i);
+    }
+    uint32_t inn = P & ~Pc;
+    while (inn) {
+      const int i = __ffs(inn) - 1;
+      inn &= inn - 1;
+      if (add(Pc, i)) Pc |= 1u << i;
+      else blocked |= 1u << i;
+    }
+    return Pc;
+  }
+  // inner loop from the feasible y (y_P > 0); t_in just entered (or -1)
+  __device__ void inner(V b, V& y, uint32_t& P, uint32_t& blocked, int t_in) {
+    bool first = true;
+#pragma unroll 1
+    for (int it = 0; it <= K + 1; ++it) {
+      if (!P) {
+        y = 0;
+        Pc = 0;
+        return;
+      }
+      const V z = apply(P, b);
+      if (first && t_in >= 0) {
+        if (!(bc(z, t_in) > (V)0)) {
+          remove(P, t_in);
+          P &= ~(1u << t_in);
+          Pc = P;
+          blocked |= 1u << t_in;
+          return;
+        }
+      }
+      first = false;
+      const uint32_t infeas = gballot(in(P) && !(z > (V)0));
+      if (!infeas) {
+        y = in(P) ? z : (V)0;
+        return;
+      }
+      V r = 2;
+      int ri = 99;
+      if ((infeas >> a) & 1u) {
+        r = y * vrcp(y - z);
+        ri = a;
+      }
+#pragma unroll
+      for (int o = 8; o >= 1; o >>= 1) {
+        const V orr = __shfl_xor_sync(gm, r, o);
+        const int oi = __shfl_xor_sync(gm, ri, o);
+        if (orr < r || (orr == r && oi < ri)) {
+          r = orr;
+          ri = oi;
+        }
+      }
+      V alpha = r;
+      int q = (r < (V)2) ? ri : -1;
+      if (q < 0) {   // only reachable through NaN: take the first infeasible one
+        alpha = 0;
+        q = __ffs(infeas) - 1;
+      }
+      if (in(P)) y = fmad(alpha, z - y, y);
+      uint32_t drop = (1u << q) | gballot(in(P) && !(y > (V)0));
+      if ((drop >> a) & 1u) y = 0;
+      while (drop) {
+        const int i = __ffs(drop) - 1;
+        drop &= drop - 1;
+        remove(P, i);
+        P &= ~(1u << i);
+      }
+      Pc = P;
+    }
+  }
+  // Full solve: y holds the warm start (lane a: component a) and the
+  // solution on exit.  Returns 0 when converged, 1 at the iteration cap.
+  __device__ int solve(V b, V& y, bool warm, uint32_t* mask_out) {
+    uint32_t blocked = 0;
+    const V bmax = gmaxv(fabs(b));
+    if (!(warm && y > (V)0)) y = 0;
+    uint32_t P = gballot(y > (V)0);
+    if (P) {
+      if (P == Pc) {
+        const V z = apply(P, b);
+        const bool feas = !gballot(in(P) && !(z > (V)0));
+        if (feas && entering(b, z, P, 0u, bmax) < 0) {
+          y = in(P) ? z : (V)0;
+          *mask_out = P;
+          return 0;
+        }
+      } else {
+        const uint32_t Q = rebase(P, blocked);
+        if (!in(Q)) y = 0;
+        P = Q;
+      }
+      if (P) inner(b, y, P, blocked, -1);
+    }
+    int status = 1;
+#pragma unroll 1
+    for (int outer = 0; outer < 5 * K + 10; ++outer) {
+      const int t = entering(b, y, P, blocked, bmax);
+      if (t < 0) {
+        status = 0;
+        break;
+      }
+      if (P != Pc) {
+        uint32_t bl2 = 0;
+        P = rebase(P, bl2);
+        blocked |= bl2;
+      }
+      if (!add(P, t)) {
+        blocked |= 1u << t;
+        continue;
+      }
+      P |= 1u << t;
+      Pc = P;
+      inner(b, y, P, blocked, t);
+    }
+    *mask_out = gballot(y > (V)0);
+    return status;
+  }
+};
+
+}  // namespace nmfgb

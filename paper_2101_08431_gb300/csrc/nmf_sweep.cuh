@@ -21,6 +21,7 @@
 
 #include "nmf_arith.cuh"
 #include "nmf_nnls.cuh"
+#include "nmf_lane16.cuh"
 
 namespace nmfgb {
 
@@ -746,7 +747,8 @@ template <typename TA, int K>
 struct XSmem {
   using Tr = XTraits<K>;
   static constexpr bool TABLE = K <= 8;
-  static constexpr int NWN = TABLE ? Tr::RB / LaneGroup<K>::CPW : 1;   // NNLS warps (k <= 8)
+  // NNLS warps: k <= 8, lane groups of KP lanes; k = 16, every warp (two rows of 16 lanes)
+  static constexpr int NWN = TABLE ? Tr::RB / LaneGroup<K>::CPW : Tr::NW;
   // warps that build the subset table of H: enough lane groups for its
   // largest level (C(k, k/2) subsets), at most half the block
   static constexpr int binom_mid() {
@@ -760,6 +762,8 @@ struct XSmem {
   // FP32), FP64 otherwise
   static constexpr bool F32NN = std::is_same<TA, float>::value && TABLE;
   using SV = typename std::conditional<F32NN, float, double>::type;
+  // k = 16: value type of the 16-lane row solves (FP32 for the FP32 pass)
+  using V16 = typename std::conditional<std::is_same<TA, float>::value, float, double>::type;
   struct Small {
     double H[K * K];
     double Gs[K * K];
@@ -770,6 +774,7 @@ struct XSmem {
     uint32_t samples[CACHE_N];
     InvCache<K> cache;
     double gram_w[NWN][K * K];
+    V16 Hp[K][K + 1];                  // k = 16: H, padded rows, in the solves' type
     double term_w[NWN][16];
     unsigned ticket;
   };
@@ -827,14 +832,6 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   } else {
     tree_sum<T>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
   }
-  if (!TABLE && tid < CACHE_N) {
-    uint32_t msk = 0;
-    if (mode == MODE_SWEEP && p.warm) {
-      const int nb = min(RB, p.n - row0);
-      msk = p.xmask[cur][row0 + (tid * nb) / CACHE_N];
-    }
-    samples[tid] = msk;
-  }
   // the first wt warps build the subset table of H while the others sum the
   // cluster partials of P
   const int wt = (TABLE && !hglob && mode == MODE_SWEEP) ? Xs::WT : 0;
@@ -880,9 +877,6 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   __syncthreads();
   NnlsSolver<K> solver;
   solver.init(H, 2.220446049250313e-16);
-  if constexpr (!TABLE) {
-    if (mode == MODE_SWEEP) build_cache<K>(&cache, solver, samples, CACHE_N);
-  }
 
   if constexpr (TABLE) {
     // lanes <-> (row slot jj, component a): warps 0 .. NWN-1 hold the 32 rows
@@ -1021,96 +1015,100 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       p.Xpart[(size_t)blk * NV + e] = r;
     }
     __threadfence();
-  } else if (warp == 0) {   // k = 16
-    double v[Tr::NVC * 32];
-#pragma unroll
-    for (int e = 0; e < Tr::NVC * 32; ++e) v[e] = 0.0;
-    if (active) {
-      double pr[K], xo[K], xn[K];
-#pragma unroll
-      for (int a = 0; a < K; ++a) {
-        TA ts = psum[0][lane][a];
-        for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lane][a]);
-        pr[a] = PartOps<TA>::to_double(ts);
-        xo[a] = p.X[cur][(size_t)row * K + a];
-        xn[a] = xo[a];
-      }
-      uint32_t msk = 0;
-      int stt = 0;
+  } else {
+    // k = 16: lane groups of 16 (lane a <-> component a), one row per group,
+    // rows 2 w and 2 w + 1 on warp w; warm-started Lawson-Hanson on the group
+    using V16 = typename Xs::V16;
+    constexpr bool F16 = std::is_same<V16, float>::value;
+    auto& gram_w = xs.gram_w;
+    auto& term_w = xs.term_w;
+    for (int e = tid; e < K * K; e += T) xs.Hp[e / K][e % K] = (V16)H[e];
+    __syncthreads();
+    const int half = lane >> 4, a = lane & 15;
+    const int lrow = warp * 2 + half, grow_i = row0 + lrow;
+    const bool ract = grow_i < p.n;   // uniform on the 16 lanes of a row
+    LaneNnls16<V16> nn;
+    nn.init(xs.Hp, F16 ? (V16)1.1920928955078125e-07 : (V16)2.220446049250313e-16);
+    double pr = 0.0, xo = 0.0;
+    uint32_t old_mask = 0;
+    if (ract) {
+      TA ts = psum[0][lrow][a];
+      for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][a]);
+      pr = PartOps<TA>::to_double(ts);
+      xo = p.X[cur][(size_t)grow_i * K + a];
+      old_mask = p.xmask[cur][grow_i];
+    }
+    double xn = xo;
+    uint32_t msk = 0;
+    int stt = 0;
+    if (ract) {
       if (mode == MODE_SWEEP) {
-        stt = -1;
-        // k = 16 (no table): the incremental solver
-        if (stt < 0) {
-          double Ascr[K * K];
-#pragma unroll
-          for (int a = 0; a < K; ++a) xn[a] = xo[a];
-          stt = solver.solve(Ascr, pr, xn, p.warm != 0, TABLE ? nullptr : &cache, &msk);
-        }
+        V16 xv = (V16)xo;
+        stt = nn.solve((V16)pr, xv, p.warm != 0, &msk);
+        xn = (double)xv;
       } else {
-#pragma unroll
-        for (int a = 0; a < K; ++a)
-          if (xo[a] > 0.0) msk |= 1u << a;
-      }
-      // X-half KKT terms of the iterate leaving this sweep: graX = H x - P
-      double neg = 0.0, comp = 0.0, pn = 0.0, xmax = 0.0, xn2 = 0.0, dx2 = 0.0, xp = 0.0;
-#pragma unroll
-      for (int a = 0; a < K; ++a) {
-        const double g = dot_masked<K>(H + a * K, xn, 0xffffffffu) - pr[a];
-        const double mn = dminz(g), pos = dmaxz(g) * xn[a];
-        neg = fmad(mn, mn, neg);
-        comp = fmad(pos, pos, comp);
-        pn = fmad(pr[a], pr[a], pn);
-        xmax = dmax_nn(xmax, xn[a]);
-        xn2 = fmad(xn[a], xn[a], xn2);
-        dx2 = fmad(xn[a] - xo[a], xn[a] - xo[a], dx2);
-        xp = fmad(xn[a], pr[a], xp);
-        if (!isfinite(pr[a])) set_err(st, ERR_NONFINITE);
-      }
-#pragma unroll
-      for (int a = 0; a < K; ++a)
-#pragma unroll
-        for (int c = 0; c < K; ++c) v[a * K + c] = xn[a] * xn[c];
-      v[K * K + XT_NEG] = neg;
-      v[K * K + XT_COMP] = comp;
-      v[K * K + XT_PNORM2] = pn;
-      v[K * K + XT_XMAX] = xmax;
-      v[K * K + XT_XNORM2] = xn2;
-      v[K * K + XT_DX2] = dx2;
-      v[K * K + XT_XP] = xp;
-      v[K * K + XT_CHANGED] = (mode == MODE_SWEEP && p.xmask[cur][row] != msk) ? 1.0 : 0.0;
-      v[K * K + XT_NOTCONV] = (double)stt;
-      if (mode == MODE_SWEEP) {
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          const float hi = __double2float_rn(xn[a]);
-          p.X[nxt][(size_t)row * K + a] = xn[a];
-          p.X32[nxt][(size_t)row * K + a] = hi;
-          p.X32lo[nxt][(size_t)row * K + a] = __double2float_rn(xn[a] - (double)hi);
-        }
-        p.xmask[nxt][row] = msk;
-      } else {
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          const float hi = __double2float_rn(xo[a]);
-          p.X32[cur][(size_t)row * K + a] = hi;
-          p.X32lo[cur][(size_t)row * K + a] = __double2float_rn(xo[a] - (double)hi);
-        }
-        p.xmask[cur][row] = msk;
+        msk = (__ballot_sync(nn.gm, dpos(xo)) >> nn.base) & 0xFFFFu;
       }
     }
-    // block partial: max for XT_XMAX, sums for the rest (fixed lane order)
-    {
-      const double mx = warp_max(v[K * K + XT_XMAX]);
-      v[K * K + XT_XMAX] = 0.0;
+    // X-half KKT terms of the iterate leaving this sweep: graX = H x - P;
+    // Gram partial: row a of x x^T
+    double gx = -pr;
+    double gr[K];
 #pragma unroll
-      for (int c = 0; c < Tr::NVC; ++c) {
-        double chunk[32];
+    for (int c = 0; c < K; ++c) {
+      const double xc = __shfl_sync(nn.gm, xn, nn.base + c);
+      gx = fmad(H[a * K + c], xc, gx);
+      gr[c] = ract ? xn * xc : 0.0;
+    }
+    __syncwarp();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) chunk[i] = v[c * 32 + i];
-        const double r = warp_reduce_scatter<32, double>(chunk);
-        const int e = c * 32 + lane;
-        if (e < NV) p.Xpart[(size_t)blk * NV + e] = (e == K * K + XT_XMAX) ? mx : r;
+    for (int c = 0; c < K; ++c) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], 16);
+    if (lane < 16) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) gram_w[warp][a * K + c] = gr[c];
+    }
+    double tv[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tv[e] = 0.0;
+    if (ract) {
+      const double mn = dminz(gx), pos = dmaxz(gx) * xn;
+      tv[XT_NEG] = mn * mn;
+      tv[XT_COMP] = pos * pos;
+      tv[XT_PNORM2] = pr * pr;
+      tv[XT_XMAX] = xn;
+      tv[XT_XNORM2] = xn * xn;
+      tv[XT_DX2] = (xn - xo) * (xn - xo);
+      tv[XT_XP] = xn * pr;
+      if (!isfinite(pr)) set_err(st, ERR_NONFINITE);
+      if (a == 0) {
+        tv[XT_CHANGED] = (mode == MODE_SWEEP && old_mask != msk) ? 1.0 : 0.0;
+        tv[XT_NOTCONV] = (double)stt;
       }
+    }
+    const double mx = warp_max(tv[XT_XMAX]);
+    tv[XT_XMAX] = 0.0;
+    const double tr = warp_reduce_scatter<16, double>(tv);
+    if (lane < 16) term_w[warp][lane] = (lane == XT_XMAX) ? mx : tr;
+    if (ract) {
+      const int xb = mode == MODE_SWEEP ? nxt : cur;
+      const double xv = mode == MODE_SWEEP ? xn : xo;
+      const float hi = __double2float_rn(xv);
+      if (mode == MODE_SWEEP) p.X[nxt][(size_t)grow_i * K + a] = xn;
+      p.X32[xb][(size_t)grow_i * K + a] = hi;
+      p.X32lo[xb][(size_t)grow_i * K + a] = __double2float_rn(xv - (double)hi);
+      if (a == 0) p.xmask[xb][grow_i] = msk;
+    }
+    __syncthreads();
+    // block partial in fixed order over the warps
+    for (int e = tid; e < NV; e += T) {
+      double r = 0.0;
+      if (e < K * K) {
+        for (int w = 0; w < NW; ++w) r += gram_w[w][e];
+      } else {
+        const int te = e - K * K;
+        for (int w = 0; w < NW; ++w) r = (te == XT_XMAX) ? dmax_nn(r, term_w[w][te]) : r + term_w[w][te];
+      }
+      p.Xpart[(size_t)blk * NV + e] = r;
     }
     __threadfence();
   }

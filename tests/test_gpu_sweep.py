@@ -69,7 +69,7 @@ def _masks_agree(vals_gpu, mask_gpu, vals_ref, rel_tol):
 
 CASES = [  # (n, m, k) -- several tiles, ragged tails, rows not a multiple of 32
     (1000, 300, 4), (777, 123, 3), (1500, 257, 8), (333, 64, 1), (2100, 190, 5),
-    (450, 97, 2), (640, 130, 6), (900, 77, 7),
+    (450, 97, 2), (640, 130, 6), (900, 77, 7), (800, 100, 16),
 ]
 
 
