@@ -68,7 +68,7 @@ struct LaneNnls16 {
     V z0 = 0, z1 = 0, z2 = 0, z3 = 0;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      const V v = ((P >> c) & 1u) ? bc(b, c) : (V)0;
+      const V v = bc(b, c) * (V)((P >> c) & 1u);   // unconditional shuffle, masked by P
       if ((c & 3) == 0) z0 = fmad(A[c], v, z0);
       else if ((c & 3) == 1) z1 = fmad(A[c], v, z1);
       else if ((c & 3) == 2) z2 = fmad(A[c], v, z2);

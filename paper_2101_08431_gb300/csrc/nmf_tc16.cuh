@@ -424,8 +424,11 @@ __global__ void __launch_bounds__(NT, 1) ypass_tc16_kernel(Problem p, int mode, 
         timed_out = true;
         break;
       }
-      double bd = 0.0;
-      for (int src = 0; src < C; ++src) bd += (double)sm.xchg[gid][gs * C + src][a];
+      // the C partials in rank order, four FP32 chains (the partials are FP32
+      // tensor-core sums; this sum adds no error beyond theirs)
+      float b4[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int src = 0; src < C; ++src) b4[src & 3] += sm.xchg[gid][gs * C + src][a];
+      const double bd = (double)((b4[0] + b4[1]) + (b4[2] + b4[3]));
       double yn = yo;
       uint32_t msk = 0;
       int stt = 0;
