@@ -357,7 +357,8 @@ K16_N, K16_M, K16_K, K16_NOISE, K16_PRECOND = 8192, 16384, 16, 1e-4, 30
 def rank16_leg(args, sptr, barrier):
     """Mixed precision at scale: n=8192, m=16384, k=16, FP32 M (512 MB, > L2,
     so no flush between timed sweeps), the FP32-class pass on the tensor
-    cores (split-BF16 contractions, FP64 solves).  Timed after K16_PRECOND
+    cores (split-BF16 contractions, FP32 column and row solves, FP64 Grams
+    and KKT terms).  Timed after K16_PRECOND
     sweeps from the U[0,1] start.  Reports sweeps/s, the M pass's HBM GB/s
     against the measured peak and its issued MMA TFLOP/s.  (The error of this
     pass against the FP64 oracle, on sampled columns and rows of the same
@@ -398,7 +399,7 @@ def rank16_leg(args, sptr, barrier):
     kk = h.objective_kkt()
     h.close()
     return {"workload": "PDF-like n=8192 m=16384 k=16 (1e-4 rel. noise), FP32 M (512 MB), tensor-core "
-                        "FP32-class pass (split-BF16 tcgen05 contractions, FP64 solves)",
+                        "FP32-class pass (split-BF16 tcgen05 contractions, FP32 solves, FP64 Grams and KKT terms)",
             "state": "timed sweeps follow %d sweeps from the U[0,1] start" % K16_PRECOND,
             "l2": "inputs larger than L2 (no flush)",
             "sweeps_per_s": steps / (ms / 1e3), "ms_per_sweep": ms / steps,
