@@ -322,6 +322,8 @@ def run_ours(args):
     # ---- batched persistent form: 256 uneven problems
     if not args.skip_batch:
         out["batched"] = batched_leg(args, rank, sptr, barrier, max_over_ranks, world)
+        if not args.skip_batch_ttk and world == 1:
+            out["batched"]["time_to_kkt_subset"] = batched_ttk_leg(args, sptr)
     # ---- streaming serving: 32 streams, Poisson chunk arrivals
     if not args.skip_serve:
         out["serving"] = serving_leg(args, rank, sptr)
@@ -476,6 +478,70 @@ def batched_leg(args, rank, sptr, barrier, max_over_ranks, world):
     return res
 
 
+BTTK_N, BTTK_MAX = 8, 30000
+
+
+def batched_ttk_leg(args, sptr):
+    """Time to relative KKT 1e-8 from the U[0,1] start for the first BTTK_N
+    problems of the batched workload: the mixed-precision batched form (one
+    batch, device-driven FP32 -> compensated schedule) against the plain FP64
+    GPU form (one FP64 handle per problem, each on its own stream, driven
+    concurrently from host threads).  Wall time of each whole run."""
+    import threading
+    import torch
+    import synth
+    from paper_2101_08431_gb300 import NMF_PREC_FP64, StreamingNMF, StreamingNMFBatch
+    shapes = synth.batch_problem_shapes(BATCH_NPROB)[:BTTK_N]
+    data = []
+    for n, m, k, seed in shapes:
+        M, _, _ = synth.pdf_like(n, m, k, noise=NOISE, relative=True, seed=seed)
+        X, Y = synth.init_factors(n, m, k, seed=seed)
+        data.append((np.asfortranarray(M, dtype=np.float32), X, Y))
+    b = StreamingNMFBatch([(n, k, m) for n, m, k, _ in shapes], kkt_target=1e-8, max_sweeps=BTTK_MAX, stream=sptr)
+    for j, (M32, X, Y) in enumerate(data):
+        b.append_columns(j, M32)
+        b.set_factors(j, X, Y)
+    b.set_pass_mode(-1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats, nrun = b.sweep(0, allow_notconv=True)
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t0
+    b.close()
+    streams = [torch.cuda.Stream() for _ in shapes]
+    hs = []
+    for (n, m, k, _), (M32, X, Y), s in zip(shapes, data, streams):
+        h = StreamingNMF(n, k, m, prec=NMF_PREC_FP64, kkt_target=1e-8, max_sweeps=BTTK_MAX, stream=s.cuda_stream)
+        h.append_columns(M32.astype(np.float64))
+        h.set_factors(X, Y)
+        hs.append(h)
+    torch.cuda.synchronize()
+    out = [None] * len(hs)
+
+    def run(i):
+        out[i] = hs[i].sweep(0, allow_notconv=True)
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(len(hs))]
+    t0 = time.perf_counter()
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    fd = max(abs(s["f"] - o["f"]) / max(abs(o["f"]), 1e-300) for s, o in zip(stats, out))
+    return {"problems": "the first %d problems of the batched workload, from the U[0,1] start" % BTTK_N,
+            "mixed_batched": {"seconds": t_mixed, "converged": sum(1 for s in stats if s["converged"] == 1),
+                              "sweeps": [s["sweeps"] for s in stats],
+                              "max_kkt_rel": max(s["kkt_rel"] for s in stats)},
+            "fp64_handles": {"seconds": t_fp64, "converged": sum(1 for o in out if o["converged"] == 1),
+                             "sweeps": [o["sweeps"] for o in out],
+                             "max_kkt_rel": max(o["kkt_rel"] for o in out)},
+            "max_rel_f_difference": fd, "sweep_cap": BTTK_MAX}
+
+
 SERVE_STREAMS, SERVE_N, SERVE_K, SERVE_CAP = 32, 2048, 6, 8192
 SERVE_RATE, SERVE_INIT = 200.0, 256
 
@@ -619,6 +685,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-problem batched leg")
     ap.add_argument("--skip-serve", action="store_true", help="skip the streaming-serving leg")
     ap.add_argument("--skip-k16", action="store_true", help="skip the rank-16 tensor-core leg")
+    ap.add_argument("--skip-batch-ttk", action="store_true",
+                    help="skip the batched-vs-FP64 time to relative KKT 1e-8 on a subset of the batch")
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--batch-ttk", action="store_true",
                     help="also run every batched problem to relative KKT 1e-8")

@@ -184,3 +184,34 @@ def test_tc16_full_size_sampled():
           % (ey, bar_y, ex, bar_x, kk["f"], f_or))
     assert ey <= bar_y and ex <= bar_x, (ey, bar_y, ex, bar_x)
     assert abs(kk["f"] - f_or) <= 1e-3 * abs(f_or)
+
+
+def test_tc16_ring_eviction_window():
+    """Streaming append past the ring capacity: the resident window wraps
+    around the ring's end (head != 0), so the converters and the column solves
+    address physical columns through the ring; one sweep on the window against
+    the oracle's sweep of the same window."""
+    S = _lib()
+    n, k, mcap = 1000, 16, 64
+    M, _, _ = synth.pdf_like(n, 80, k, noise=1e-3, relative=True, seed=8)
+    M32 = np.asfortranarray(M.astype(np.float32))
+    W64 = M32[:, 16:80].astype(np.float64)          # the newest 64 columns
+    X, Y = synth.init_factors(n, mcap, k, seed=8)
+    X, Y, _, _, _, _, st = oracle.anls(W64, X, Y, max_sweeps=10)
+    assert st == oracle.OK
+    X, Y = np.ascontiguousarray(X), np.ascontiguousarray(Y)
+    Xo, Yo, _, _, st = oracle.sweep(W64, X, Y)
+    h = S(n, k, mcap, prec=1, kkt_target=0.0)
+    h.append_columns(np.asfortranarray(M32[:, :40]))
+    h.append_columns(np.asfortranarray(M32[:, 40:80]))   # evicts the 16 oldest; the window wraps
+    assert h.m == mcap
+    h.set_factors(X, Y)
+    h.set_pass_mode(0)
+    h.sweep(1)
+    Xg, Yg, _, _ = h.get_factors()
+    h.close()
+    bar_y = max(5e-4, 3e-5 * np.linalg.cond(X.T @ X))
+    bar_x = max(5e-4, 3e-5 * np.linalg.cond(Yo @ Yo.T))
+    ey, ex = _rel(Yg, Yo), _rel(Xg, Xo)
+    print("ring window: rel err Y %.2e (bar %.1e) X %.2e (bar %.1e)" % (ey, bar_y, ex, bar_x))
+    assert ey <= bar_y and ex <= bar_x
