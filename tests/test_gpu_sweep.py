@@ -1,6 +1,8 @@
 """GPU parity of the ANLS sweep against the CPU oracle, through the C ABI.
 
-Bars (derived in the design doc):
+Bars (the rounding of each pass's contraction, ~1e-16 FP64, ~1e-13
+double-float, ~1e-7 FP32 relative, amplified by the condition number of the
+half-sweep's Gram, with margin):
 * FP64 form and FP64-accumulated passes: one sweep from the same state
   agrees with the oracle to relative 1e-10 (Frobenius) on X and Y, and the
   passive sets agree except on degenerate entries;
