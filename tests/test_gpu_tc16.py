@@ -4,11 +4,12 @@ contractions, FP64 column solves), through the C ABI.
 The FP32-class pass of the mixed form at k = 16 runs B = X^T M and P = M Y^T
 as (M_hi + M_lo)(V_hi + V_lo) BF16 products with FP32 accumulation.  Each of
 hi, lo carries 8 significant bits, so the pair represents a value to within
-2^-18 of its magnitude; the products and the FP32 sums of a contraction of
-length L then carry a relative error of about 2 * 2^-18 + L^(1/2) 2^-24
-(< 1e-5 for the sizes here).  A half-sweep amplifies the error of its
-right-hand side by the condition number of its Gram (G = X^T X for Y,
-H = Y Y^T for X), so the bar of one sweep is max(5e-4, 3e-5 cond).
+2^-16 of its magnitude (typically ~2^-18); a product of two split values is
+then within 2 * 2^-16 ~ 3.05e-5, and the FP32 sums of a contraction of length
+L add about L^(1/2) 2^-24 (tests/test_split_bf16_bound.py checks both).  A
+half-sweep amplifies the error of its right-hand side by the condition number
+of its Gram (G = X^T X for Y, H = Y Y^T for X), so the bar of one sweep is
+max(5e-4, 3e-5 cond).
 
 Shapes cover a single CTA per column range (C = 1), clusters of 2, 4 and 16
 CTAs (rows split), CTAs that own no rows, a ragged last tile of columns and
