@@ -216,3 +216,29 @@ def test_tc16_ring_eviction_window():
     ey, ex = _rel(Yg, Yo), _rel(Xg, Xo)
     print("ring window: rel err Y %.2e (bar %.1e) X %.2e (bar %.1e)" % (ey, bar_y, ex, bar_x))
     assert ey <= bar_y and ex <= bar_x
+
+
+def test_tc16_graph_replay_matches_plain_launches():
+    """Sweeps in chunks of 32 are captured into a CUDA graph the second time
+    their signature is seen and replayed after that; the tensor-core pass's
+    cluster launches must give bitwise the same iterates replayed as launched
+    one sweep at a time (every partition and reduction order is fixed)."""
+    S = _lib()
+    n, m = 700, 150
+    M32, M64, X, Y = _warm_state(n, m, 2, sweeps=4)
+    out = []
+    for chunked in (True, False):
+        h = S(n, 16, m, prec=1, kkt_target=0.0)
+        h.append_columns(M32)
+        h.set_factors(X, Y)
+        h.set_pass_mode(0)
+        if chunked:
+            h.sweep(96)          # chunk 1 plain, chunk 2 captured, chunk 3 replayed
+        else:
+            for _ in range(96):
+                h.sweep(1)
+        out.append(h.get_factors())
+        h.close()
+    (Xa, Ya, xa, ya), (Xb, Yb, xb, yb) = out
+    assert np.array_equal(Xa, Xb) and np.array_equal(Ya, Yb)
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
