@@ -299,6 +299,14 @@ nmf_status nmf_batch_autotune(nmf_batch *b, int32_t trial_sweeps, int32_t *cols_
  * The paper has no counterpart; no kernel of the library spins unbounded. */
 nmf_status nmf_selftest_bounded_wait(int64_t polls, void *cuda_stream);
 
+/* Self-test of the bounded wait of the rank-16 tensor-core M pass: one kernel
+ * waits, through that pass's wait function, on an mbarrier nothing arrives
+ * on, with a wall-time limit of limit_ms (1..10000; the pass itself uses
+ * 2000).  Returns NMF_ETIMEOUT when the wait gave up and raised the pass's
+ * abort flag (the expected outcome), NMF_OK if it ended otherwise, NMF_EINVAL
+ * for a bad limit.  The paper has no counterpart. */
+nmf_status nmf_selftest_tc16_wait(int64_t limit_ms, void *cuda_stream);
+
 /* Kernel launches issued by the batch (graph replays count their launches). */
 int64_t nmf_batch_launch_count(const nmf_batch *b);
 const char *nmf_batch_last_error(const nmf_batch *b);

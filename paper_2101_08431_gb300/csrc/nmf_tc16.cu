@@ -1,4 +1,5 @@
 // Host side of the rank-16 tensor-core M pass: launch plan and launch.
+#include "nmf.h"
 #include "nmf_tc16.cuh"
 
 namespace nmfgb {
@@ -91,4 +92,47 @@ cudaError_t tc16_launch(const Problem& p, int mode, const Tc16Plan& L, cudaStrea
   return cudaLaunchKernelEx(&cfg, tc16::ypass_tc16_kernel, p, mode, L);
 }
 
+namespace {
+
+// One warp waits, through the rank-16 pass's own bounded wait, on an mbarrier
+// that nothing arrives on; out[0] = 1 when the wait gave up, out[1] = the
+// abort flag it raised for the other roles.
+__global__ void tc16_wait_selftest_kernel(unsigned long long limit_ns, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = tc16::bwait_flag<false>(&abort_flag, &bar, 0u, limit_ns);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = ok ? 0 : 1;
+    out[1] = abort_flag;
+    mbar_inval(&bar);
+  }
+}
+
+}  // namespace
+
 }  // namespace nmfgb
+
+extern "C" nmf_status nmf_selftest_tc16_wait(int64_t limit_ms, void* cuda_stream) {
+  if (limit_ms < 1 || limit_ms > 10000) return NMF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int* d = nullptr;
+  int h[2] = {0, 0};
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return NMF_ENOMEM;
+  nmf_status out = NMF_ECUDA;
+  if (cudaMemsetAsync(d, 0, 2 * sizeof(int), s) == cudaSuccess) {
+    nmfgb::tc16_wait_selftest_kernel<<<1, 32, 0, s>>>((unsigned long long)limit_ms * 1000000ull, d);
+    if (cudaGetLastError() == cudaSuccess &&
+        cudaMemcpyAsync(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess)
+      out = (h[0] == 1 && h[1] == 1) ? NMF_ETIMEOUT : NMF_OK;
+  }
+  cudaFree(d);
+  return out;
+}

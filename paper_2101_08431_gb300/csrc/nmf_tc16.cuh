@@ -119,32 +119,29 @@ __device__ __forceinline__ unsigned long long gtime() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool aborted(Small& sm) { return *reinterpret_cast<volatile int*>(&sm.abort_flag) != 0; }
-// Bounded waits: false after WAIT_NS, or as soon as another role of the CTA
-// has given up (which it announces through abort_flag).
-__device__ __forceinline__ bool bwait(Small& sm, uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool flag_set(int* flag) { return *reinterpret_cast<volatile int*>(flag) != 0; }
+__device__ __forceinline__ bool aborted(Small& sm) { return flag_set(&sm.abort_flag); }
+// Bounded waits: false after WAIT_NS (limit_ns), or as soon as another role of
+// the CTA has given up (which it announces through *abort_flag).
+template <bool CLUSTER>
+__device__ __forceinline__ bool bwait_flag(int* abort_flag, uint64_t* bar, uint32_t parity,
+                                           unsigned long long limit_ns = WAIT_NS) {
   const unsigned long long t0 = gtime();
   for (unsigned i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 63) {
-      if (aborted(sm)) return false;
-      if (gtime() - t0 > WAIT_NS) break;
+      if (flag_set(abort_flag)) return false;
+      if (gtime() - t0 > limit_ns) break;
     }
   }
-  atomicExch(&sm.abort_flag, 1);
+  atomicExch(abort_flag, 1);
   return false;
 }
+__device__ __forceinline__ bool bwait(Small& sm, uint64_t* bar, uint32_t parity) {
+  return bwait_flag<false>(&sm.abort_flag, bar, parity);
+}
 __device__ __forceinline__ bool bwait_cluster(Small& sm, uint64_t* bar, uint32_t parity) {
-  const unsigned long long t0 = gtime();
-  for (unsigned i = 0;; ++i) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((i & 63) == 63) {
-      if (aborted(sm)) return false;
-      if (gtime() - t0 > WAIT_NS) break;
-    }
-  }
-  atomicExch(&sm.abort_flag, 1);
-  return false;
+  return bwait_flag<true>(&sm.abort_flag, bar, parity);
 }
 
 __device__ __forceinline__ void st_remote_f32(float* local_addr, int rank, float v) {

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "nmf.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(nmf_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(nmf_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -98,3 +98,5 @@ def test_selftest_rejects_bad_limit(lib):
     from paper_2101_08431_gb300 import _native
     assert lib.nmf_selftest_bounded_wait(0, None) == _native.NMF_EINVAL
     assert lib.nmf_selftest_bounded_wait(1 << 30, None) == _native.NMF_EINVAL
+    assert lib.nmf_selftest_tc16_wait(0, None) == _native.NMF_EINVAL
+    assert lib.nmf_selftest_tc16_wait(20000, None) == _native.NMF_EINVAL

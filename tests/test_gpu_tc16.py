@@ -242,3 +242,20 @@ def test_tc16_graph_replay_matches_plain_launches():
     (Xa, Ya, xa, ya), (Xb, Yb, xb, yb) = out
     assert np.array_equal(Xa, Xb) and np.array_equal(Ya, Yb)
     assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+
+
+def test_tc16_bounded_wait_reports_timeout():
+    """The rank-16 pass's wait gives up after its wall-time limit on an
+    mbarrier nothing arrives on, raises its abort flag and returns
+    NMF_ETIMEOUT; the context stays usable."""
+    _lib()
+    import time
+    import torch
+    from paper_2101_08431_gb300 import _native
+    L = _native.load()
+    t0 = time.time()
+    assert L.nmf_selftest_tc16_wait(200, None) == _native.NMF_ETIMEOUT
+    dt = time.time() - t0
+    assert 0.15 < dt < 30.0, dt
+    x = torch.ones(16, device="cuda")
+    assert float(x.sum().item()) == 16.0        # the device still answers
