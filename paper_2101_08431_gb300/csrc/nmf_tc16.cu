@@ -42,30 +42,40 @@ int pow2ceil(int v) {
 
 }  // namespace
 
+bool tc16_shape(int ld, int C, int smem_optin, Tc16Plan* out) {
+  using namespace tc16;
+  if (ld < 1 || C < 1 || C > 16 || (C & (C - 1)) != 0) return false;
+  const size_t small = small_bytes();
+  const int R = (ld + C - 1) / C;
+  const int Rr = (R + 127) / 128 * 128;
+  const long long room = (long long)smem_optin - (long long)small - (long long)ax_bytes(Rr);
+  if (room <= 0) return false;
+  int NS = (int)(room / (long long)slot_bytes(Rr));
+  if (NS > NSMAX) NS = NSMAX;
+  if (NS < 2) return false;
+  const int tcols = pow2ceil(std::max(32, NS * 32 + (Rr / 128) * 16));
+  if (tcols > 512) return false;
+  Tc16Plan L{};
+  L.C = C;
+  L.R = Rr;
+  L.NS = NS;
+  L.Q = 0;
+  L.tmem_cols = tcols;
+  L.smem = small + ax_bytes(Rr) + (size_t)NS * slot_bytes(Rr);
+  *out = L;
+  return true;
+}
+
 bool tc16_plan(int ld, int m, int nsm, int smem_optin, Tc16Plan* out) {
   using namespace tc16;
   tc16_set_attr();
-  const size_t small = small_bytes();
   Tc16Plan best{};
   bool have = false;
   for (int C = 1; C <= 16; C <<= 1) {
-    const int R = (ld + C - 1) / C;
-    const int Rr = (R + 127) / 128 * 128;
-    const long long room = (long long)smem_optin - (long long)small - (long long)ax_bytes(Rr);
-    if (room <= 0) continue;
-    int NS = (int)(room / (long long)slot_bytes(Rr));
-    if (NS > NSMAX) NS = NSMAX;
-    if (NS < 2) continue;
-    const int tcols = pow2ceil(std::max(32, NS * 32 + (Rr / 128) * 16));
-    if (tcols > 512) continue;
     Tc16Plan L{};
-    L.C = C;
-    L.R = Rr;
-    L.NS = NS;
-    L.tmem_cols = tcols;
-    L.smem = small + ax_bytes(Rr) + (size_t)NS * slot_bytes(Rr);
-    L.Q = 1;
+    if (!tc16_shape(ld, C, smem_optin, &L)) continue;
     cudaLaunchAttribute at[1];
+    L.Q = 1;
     cudaLaunchConfig_t cfg = tc16_config(L, at);
     int fit = 0;
     if (cudaOccupancyMaxActiveClusters(&fit, (const void*)ypass_tc16_kernel, &cfg) != cudaSuccess) {
@@ -78,7 +88,7 @@ bool tc16_plan(int ld, int m, int nsm, int smem_optin, Tc16Plan* out) {
     (void)nsm;
     best = L;
     have = true;
-    if (NS >= 4) break;   // the smallest cluster with a ring of four tiles
+    if (L.NS >= 4) break;   // the smallest cluster with a ring of four tiles
   }
   if (have) *out = best;
   return have;
