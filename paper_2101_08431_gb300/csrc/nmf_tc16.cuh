@@ -7,7 +7,9 @@
 // Precision: M (FP32 in HBM), X and Y are split into BF16 pairs
 // v = hi + lo (hi = bf16(v), lo = bf16(v - hi)); both contractions are
 // (M_hi + M_lo)(V_hi + V_lo) as BF16 x BF16 products with FP32 accumulation
-// in tensor memory.  The column solves, G, H and the KKT terms are FP64.
+// in tensor memory.  The column solves run in FP32 (this pass's B is good
+// to ~1e-5, far above FP32 rounding of the solve); G, H and the KKT terms
+// are FP64.
 //
 // Partition.  A cluster of C CTAs covers all rows of M: CTA r owns the rows
 // [r R, r R + R) (R a multiple of 128).  Cluster q owns a contiguous range
@@ -20,9 +22,10 @@
 //   B epilogue       reads D_B (rows 0-15: X_hi, 16-31: X_lo), adds the
 //                    four partial products and pushes column j's partial
 //                    to the CTA that owns column j (rank j mod C);
-//   NNLS warp        sums the C partials of its columns in rank order (FP64),
-//                    solves each column with a 16-lane Lawson-Hanson and
-//                    sends y (FP32) to every CTA of the cluster;
+//   solve groups     four 16-lane groups (warps 1 and 3) sum the C partials
+//                    of their columns in rank order, solve each column with a
+//                    warm-started Lawson-Hanson and send y (FP32) to every CTA
+//                    of the cluster, then form the KKT terms and H;
 //   Y builder        splits the tile's y into the BF16 operand of the P-MMA;
 //   MMA thread       P-MMA: D_P(128 x 16 per 128-row chunk) +=
 //                    [M_hi, M_lo] (A, M-major) x [Y_hi, Y_lo] (B, K-major);
@@ -30,8 +33,9 @@
 // A ring of NS slots holds each converted tile from its B-MMA to its P-MMA,
 // so the stream of M continues while the columns of earlier tiles are being
 // solved; M is read from HBM exactly once.  The B-MMA uses M = 64 rows of
-// which 32 carry X: rows 32-63 read the next core matrices of the slab (a
-// layout choice that needs no zero padding) and are discarded.
+// which 32 carry X: rows 32-63 read the next core matrices of the slab (whose
+// 512-byte zero pad keeps the last K-step's reads in bounds) and are
+// discarded.
 //
 // Every wait is bounded; on a timeout the CTA raises ERR_TIMEOUT, stops its
 // loops, drains its MMAs and frees its tensor memory before returning.
