@@ -771,8 +771,6 @@ struct XSmem {
     TA psum[Tr::NW][Tr::RB][K];
     double fin[Tr::NV];
     double yfin[NYT];
-    uint32_t samples[CACHE_N];
-    InvCache<K> cache;
     double gram_w[NWN][K * K];
     V16 Hp[K][K + 1];                  // k = 16: H, padded rows, in the solves' type
     double term_w[NWN][16];
@@ -788,7 +786,7 @@ struct XSmem {
 // partials of P = M Y^T (lane <-> row, summed in the partials' own type) and
 // build the subset table of H; k <= 8: 32 / CPW warps solve the 32 row NNLS
 // problems lane-parallel (lane <-> (row, component)) and form the X-half
-// terms and the Gram partial (k = 16: warp 0, one row per lane); the last
+// terms and the Gram partial (k = 16: every warp, one row per 16-lane group); the last
 // block to finish combines the blocks, forms G = X^T X (and its subset table
 // for k = 7, 8), and the statistics of the iterate.
 //
@@ -815,8 +813,6 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   auto& psum = xs.psum;
   double* fin = xs.fin;
   double* yfin = xs.yfin;
-  uint32_t* samples = xs.samples;
-  InvCache<K>& cache = xs.cache;
   unsigned& ticket = xs.ticket;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   DevState* st = p.st;
