@@ -47,6 +47,7 @@ def lib():
         L = _lib
         i64, i32, d = C.c_int64, C.c_int, C.c_double
         L.oracle_nnls.argtypes = [i32, _dp, _dp, _dp, _up, C.POINTER(C.c_int)]
+        L.oracle_nnls_warm.argtypes = [i32, _dp, _dp, _dp, _up, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.oracle_sweep.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _up, _up, C.POINTER(C.c_int64)]
         L.oracle_grad.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp, _dp]
         L.oracle_grad.restype = d
@@ -93,6 +94,21 @@ def nnls(G, b):
     it = C.c_int(0)
     st = lib().oracle_nnls(k, _p(G), _p(b), _p(y), C.byref(mask), C.byref(it))
     return y, mask.value, it.value, st
+
+
+def nnls_warm(G, b, y0):
+    """Warm-started Lawson-Hanson from the support of y0 (Sec. 2's reuse of the
+    previous problem's solution).  Returns (y, passive mask, entering steps,
+    passive-set changes, status)."""
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    y = np.ascontiguousarray(np.maximum(np.asarray(y0, dtype=np.float64), 0.0)).copy()
+    k = b.shape[0]
+    mask = C.c_uint32(0)
+    it = C.c_int(0)
+    ch = C.c_int(0)
+    st = lib().oracle_nnls_warm(k, _p(G), _p(b), _p(y), C.byref(mask), C.byref(it), C.byref(ch))
+    return y, mask.value, it.value, ch.value, st
 
 
 def sweep(M, X, Y):

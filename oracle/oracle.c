@@ -171,6 +171,112 @@ int oracle_nnls(int k, const double *G, const double *b, double *y,
     return status;
 }
 
+/* Warm-started Lawson-Hanson (Sec. 2: the solution of the previous problem
+ * seeds the next one, e.g. column j - 1 for column j).  y holds the warm start
+ * on entry (y >= 0; its support is the initial passive set) and the solution
+ * on exit.  The method is the cold-start solver's from a feasible point: the
+ * inner loop first steps from y towards the least-squares solution on the
+ * warm passive set, dropping variables that reach zero, then the outer loop
+ * adds entering variables as before (same tolerance, ties, blocking and cap).
+ * *outer_out: entering steps taken; *changes_out: variables that entered or
+ * left the passive set.  The solution is unique (G positive definite), so it
+ * agrees with the cold solve up to rounding; only the work differs. */
+int oracle_nnls_warm(int k, const double *G, const double *b, double *y,
+                     uint32_t *mask_out, int *outer_out, int *changes_out)
+{
+    if (k < 1 || k > KMAX) return OR_EINVAL;
+    double gmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+        if (!isfinite(b[i])) return OR_ENUMERIC;
+        if (G[i * k + i] > gmax) gmax = G[i * k + i];
+    }
+    const double pivot_min = 1e-14 * gmax;
+    uint32_t P = 0, blocked = 0;
+    int changes = 0;
+    for (int i = 0; i < k; ++i) {
+        if (y[i] > 0.0) P |= 1u << i;
+        else y[i] = 0.0;
+    }
+    double w[KMAX], z[KMAX];
+    int status = OR_NOTCONV, outer = 0;
+    const int cap = 5 * k + 10;
+    int t_in = -1;                  /* no entering variable on the first pass */
+    for (;;) {
+        /* inner loop from the feasible y on P (t_in: the variable that just entered) */
+        int first = t_in >= 0;
+        for (int inner = 0; P && inner <= k + 1; ++inner) {
+            int f = chol_solve_subset(k, G, b, P, pivot_min, z);
+            if (f >= 0) {
+                P &= ~(1u << f);
+                blocked |= 1u << f;
+                y[f] = 0.0;
+                ++changes;
+                first = 0;
+                continue;
+            }
+            if (first && !(z[t_in] > 0.0)) {
+                P &= ~(1u << t_in);
+                blocked |= 1u << t_in;
+                ++changes;
+                break;
+            }
+            first = 0;
+            int feasible = 1;
+            for (int i = 0; i < k; ++i)
+                if ((P & (1u << i)) && !(z[i] > 0.0)) feasible = 0;
+            if (feasible) {
+                for (int i = 0; i < k; ++i) y[i] = (P & (1u << i)) ? z[i] : 0.0;
+                break;
+            }
+            double alpha = 2.0;
+            int q = -1;
+            for (int i = 0; i < k; ++i) {
+                if (!(P & (1u << i)) || z[i] > 0.0) continue;
+                double a = y[i] / (y[i] - z[i]);
+                if (a < alpha) { alpha = a; q = i; }
+            }
+            for (int i = 0; i < k; ++i)
+                if (P & (1u << i)) y[i] += alpha * (z[i] - y[i]);
+            y[q] = 0.0;
+            P &= ~(1u << q);
+            ++changes;
+            for (int i = 0; i < k; ++i)
+                if ((P & (1u << i)) && !(y[i] > 0.0)) { y[i] = 0.0; P &= ~(1u << i); ++changes; }
+        }
+        if (!P)
+            for (int i = 0; i < k; ++i) y[i] = 0.0;
+        if (outer >= cap) break;
+        /* outer step: w = b - G y and the entering test */
+        double bmax = 0.0, ymax = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double s = b[i];
+            for (int l = 0; l < k; ++l) s -= G[i * k + l] * y[l];
+            w[i] = s;
+            if (fabs(b[i]) > bmax) bmax = fabs(b[i]);
+            if (y[i] > ymax) ymax = y[i];
+        }
+        const double tol = 10.0 * k * EPS64 * (bmax + gmax * ymax);
+        t_in = -1;
+        double best = tol;
+        for (int i = 0; i < k; ++i) {
+            uint32_t bit = 1u << i;
+            if ((P & bit) || (blocked & bit)) continue;
+            if (w[i] > best) { best = w[i]; t_in = i; }
+        }
+        if (t_in < 0) { status = OR_OK; break; }
+        P |= 1u << t_in;
+        ++changes;
+        ++outer;
+    }
+    uint32_t mask = 0;
+    for (int i = 0; i < k; ++i)
+        if (y[i] > 0.0) mask |= 1u << i;
+    if (mask_out) *mask_out = mask;
+    if (outer_out) *outer_out = outer;
+    if (changes_out) *changes_out = changes;
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One ANLS sweep (Alg. "anls", Sec. 2), Y-update first, then X-update:     */
 /*   Y_{:,j} = argmin_{y>=0} 1/2 ||X y - M_{:,j}||^2   for every column j;  */
