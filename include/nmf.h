@@ -109,7 +109,13 @@ void nmf_config_init(nmf_config *cfg);
  * memory up front; no allocation happens in later calls except
  * nmf_append_columns' staging of host data.  Errors: NMF_EINVAL for n < 1,
  * k outside 1..8 and 16, m_capacity < 1 or n beyond the kernels' row limit
- * (16384 rows FP32, 8192 FP64); NMF_ENOMEM; NMF_ECUDA. */
+ * (16384 rows FP32, 8192 FP64); NMF_ENOMEM; NMF_ECUDA.
+ * Rank 16 with NMF_PREC_MIXED: the FP32-class pass runs on the tensor cores
+ * (split-BF16 contractions, FP32 solves; about 1e-5 relative in B and P).
+ * Where n is beyond the rows of the FP64-class kernels at rank 16 (n above
+ * about 3840), the handle runs that pass alone: the automatic schedule never
+ * leaves it, pass modes 1 and 2 run it as well, and nmf_objective_kkt
+ * measures with it. */
 nmf_status nmf_create(const nmf_config *cfg, nmf_handle **out);
 
 /* Free every resource of the handle (NULL is accepted). */
@@ -153,6 +159,7 @@ nmf_status nmf_sweep(nmf_handle *h, int32_t nsweeps, nmf_stats *stats);
  * 2 = compensated FP32 (double-float) contraction of the FP32 M, about 44
  * significant bits; -1 = automatic: FP32 until the relative KKT error reaches
  * mixed_switch or stalls, then compensated).  NMF_PREC_FP64 handles ignore it.
+ * At rank 16, mode 0 is the tensor-core pass (see nmf_create).
  * NMF_EINVAL for any other mode. */
 nmf_status nmf_set_pass_mode(nmf_handle *h, int32_t mode);
 
