@@ -30,38 +30,57 @@ _dp = C.POINTER(C.c_double)
 _up = C.POINTER(C.c_uint32)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent)."""
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle shared library (idempotent).  openmp=True builds the
+    same source with -fopenmp into a second library, whose sweep shares the
+    independent column and row problems among the host's threads (for the
+    all-cores CPU baseline); every value it computes is the serial build's."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    lib_path = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+        tmp = lib_path + ".tmp.%d" % os.getpid()
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11"] + flags + ["-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
-def lib():
-    global _lib
+_lib_omp = None
+
+
+def lib(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            _lib_omp = _declare(C.CDLL(build(openmp=True)))
+        return _lib_omp
     if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
-        i64, i32, d = C.c_int64, C.c_int, C.c_double
-        L.oracle_nnls.argtypes = [i32, _dp, _dp, _dp, _up, C.POINTER(C.c_int)]
-        L.oracle_nnls_warm.argtypes = [i32, _dp, _dp, _dp, _up, C.POINTER(C.c_int), C.POINTER(C.c_int)]
-        L.oracle_sweep.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _up, _up, C.POINTER(C.c_int64)]
-        L.oracle_grad.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp, _dp]
-        L.oracle_grad.restype = d
-        L.oracle_objective.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp]
-        L.oracle_objective.restype = d
-        L.oracle_kkt.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp]
-        L.oracle_anls.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _up, _up, i32, d, d, _dp,
-                                  C.POINTER(C.c_int)]
-        L.oracle_ipm_direction.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp, _dp, d, d, i32,
-                                           _dp, _dp, _dp, _dp]
-        L.oracle_ipm.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, d, i32, _dp, _dp, i32,
-                                 C.POINTER(C.c_int)]
-        L.oracle_two_stage.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, d, i32, d, i32, _dp]
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(L):
+    """Argument types of the oracle's C functions on the loaded library L."""
+    i64, i32, d = C.c_int64, C.c_int, C.c_double
+    L.oracle_nnls.argtypes = [i32, _dp, _dp, _dp, _up, C.POINTER(C.c_int)]
+    L.oracle_nnls_warm.argtypes = [i32, _dp, _dp, _dp, _up, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.oracle_sweep.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _up, _up, C.POINTER(C.c_int64)]
+    L.oracle_grad.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp, _dp]
+    L.oracle_grad.restype = d
+    L.oracle_objective.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp]
+    L.oracle_objective.restype = d
+    L.oracle_kkt.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp]
+    L.oracle_anls.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _up, _up, i32, d, d, _dp,
+                              C.POINTER(C.c_int)]
+    L.oracle_ipm_direction.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, _dp, _dp, d, d, i32,
+                                       _dp, _dp, _dp, _dp]
+    L.oracle_ipm.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, d, i32, _dp, _dp, i32,
+                             C.POINTER(C.c_int)]
+    L.oracle_two_stage.argtypes = [i64, i64, i32, _dp, i64, _dp, _dp, d, i32, d, i32, _dp]
+    return L
 
 
 def _p(a):
@@ -111,8 +130,9 @@ def nnls_warm(G, b, y0):
     return y, mask.value, it.value, ch.value, st
 
 
-def sweep(M, X, Y):
-    """One ANLS sweep (Y-update, then X-update). Returns (X, Y, xmask, ymask, status)."""
+def sweep(M, X, Y, openmp=False):
+    """One ANLS sweep (Y-update, then X-update). Returns (X, Y, xmask, ymask, status).
+    openmp=True runs the -fopenmp build (columns and rows on all host threads)."""
     Mf = _colmajor(M)
     n, m = Mf.shape
     X = _xbuf(X)
@@ -121,8 +141,8 @@ def sweep(M, X, Y):
     xm = np.zeros(n, dtype=np.uint32)
     ym = np.zeros(m, dtype=np.uint32)
     nc = C.c_int64(0)
-    st = lib().oracle_sweep(n, m, k, _p(Mf), n, _p(X), _p(Y), xm.ctypes.data_as(_up),
-                            ym.ctypes.data_as(_up), C.byref(nc))
+    st = lib(openmp).oracle_sweep(n, m, k, _p(Mf), n, _p(X), _p(Y), xm.ctypes.data_as(_up),
+                                  ym.ctypes.data_as(_up), C.byref(nc))
     return X, Y, xm, ym, st
 
 

@@ -288,9 +288,9 @@ int oracle_sweep(int64_t n, int64_t m, int k, const double *M, int64_t ldm,
                  int64_t *notconv_out)
 {
     if (n < 1 || m < 1 || k < 1 || k > KMAX || ldm < n) return OR_EINVAL;
-    double G[KMAX * KMAX], b[KMAX];
+    double G[KMAX * KMAX];
     int64_t notconv = 0;
-    int st;
+    int bad = OR_OK;
     /* G = X^T X */
     for (int a = 0; a < k; ++a)
         for (int c = 0; c < k; ++c) {
@@ -298,16 +298,25 @@ int oracle_sweep(int64_t n, int64_t m, int k, const double *M, int64_t ldm,
             for (int64_t i = 0; i < n; ++i) s += X[i * k + a] * X[i * k + c];
             G[a * k + c] = s;
         }
+    /* The columns are independent problems (and so are the rows below): a
+     * build with -fopenmp shares them among threads, each column computed
+     * exactly as in the serial build; the default build ignores the pragma. */
+    #pragma omp parallel for schedule(dynamic, 16) reduction(+ : notconv)
     for (int64_t j = 0; j < m; ++j) {
+        double b[KMAX];
         for (int a = 0; a < k; ++a) {        /* b = X^T M_{:,j} */
             double s = 0.0;
             for (int64_t i = 0; i < n; ++i) s += X[i * k + a] * M[i + ldm * j];
             b[a] = s;
         }
-        st = oracle_nnls(k, G, b, Y + k * j, ymask ? ymask + j : NULL, NULL);
+        const int st = oracle_nnls(k, G, b, Y + k * j, ymask ? ymask + j : NULL, NULL);
         if (st == OR_NOTCONV) ++notconv;
-        else if (st != OR_OK) return st;
+        else if (st != OR_OK) {
+            #pragma omp critical
+            bad = st;
+        }
     }
+    if (bad != OR_OK) return bad;
     /* H = Y Y^T */
     double H[KMAX * KMAX];
     for (int a = 0; a < k; ++a)
@@ -316,16 +325,22 @@ int oracle_sweep(int64_t n, int64_t m, int k, const double *M, int64_t ldm,
             for (int64_t j = 0; j < m; ++j) s += Y[a + k * j] * Y[c + k * j];
             H[a * k + c] = s;
         }
+    #pragma omp parallel for schedule(dynamic, 16) reduction(+ : notconv)
     for (int64_t i = 0; i < n; ++i) {
+        double b[KMAX];
         for (int a = 0; a < k; ++a) {        /* b = (M Y^T)_{i,:} */
             double s = 0.0;
             for (int64_t j = 0; j < m; ++j) s += M[i + ldm * j] * Y[a + k * j];
             b[a] = s;
         }
-        st = oracle_nnls(k, H, b, X + i * k, xmask ? xmask + i : NULL, NULL);
+        const int st = oracle_nnls(k, H, b, X + i * k, xmask ? xmask + i : NULL, NULL);
         if (st == OR_NOTCONV) ++notconv;
-        else if (st != OR_OK) return st;
+        else if (st != OR_OK) {
+            #pragma omp critical
+            bad = st;
+        }
     }
+    if (bad != OR_OK) return bad;
     if (notconv_out) *notconv_out = notconv;
     return OR_OK;
 }
