@@ -4,6 +4,7 @@
 // device control block, the next iterate) lives in one file-scope
 // __device__ array of NOALLOC_SCRATCH_BYTES.  The caller passes M, X and Y;
 // X and Y are updated in place.
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -73,6 +74,20 @@ __global__ void na_msq_kernel(const double* colsq, int m, DevState* st) {
   if (threadIdx.x == 0) st->msq = red[0];
 }
 
+// Last step of a call: the statistics record of the incoming iterate (slot
+// 15: the control block's error bits, 0 when the sweep completed cleanly) and,
+// only when no error bit is set, the next iterate over the caller's X and Y.
+// With an error bit set X and Y keep the incoming iterate.
+__global__ void na_finish_kernel(const DevState* st, const double* Xn, double* X, long long nx, const double* Yn,
+                                 double* Y, long long ny, double* stats_dev) {
+  const unsigned err = st->err;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+  if (stats_dev && i0 < NSTAT) stats_dev[i0] = (i0 == NSTAT - 1) ? (double)err : st->stats[0][i0];
+  if (err) return;
+  for (long long i = i0; i < nx; i += step) X[i] = Xn[i];
+  for (long long i = i0; i < ny; i += step) Y[i] = Yn[i];
+}
+
 size_t take(size_t& off, size_t bytes) {
   const size_t at = off;
   off += (bytes + 255) & ~size_t(255);
@@ -86,6 +101,12 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   if (!M || !X || !Y || n < 1 || m < 1 || k < 1) return NMF_EINVAL;
   if (n > NA_NMAX || m > NA_MMAX || k > NA_KMAX) return NMF_ECAPACITY;
   if (ldm != ((n + 31) / 32) * 32) return NMF_EINVAL;
+  // the M pass stages column segments with bulk copies, which need a 16-byte
+  // aligned source (ldm * 4 bytes is a multiple of 128); X, Y and the record
+  // are read and written as doubles.  Checked here, before any device work.
+  if (reinterpret_cast<uintptr_t>(M) % 16 != 0 || reinterpret_cast<uintptr_t>(X) % 8 != 0 ||
+      reinterpret_cast<uintptr_t>(Y) % 8 != 0 || reinterpret_cast<uintptr_t>(stats_dev) % 8 != 0)
+    return NMF_EINVAL;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   void* base = nullptr;
   nmf_status s = scratch_for_current_device(&base);
@@ -191,13 +212,7 @@ extern "C" nmf_status nmf_sweep_noalloc(const float* M, int64_t n, int64_t m, in
   if (ks.xpass(p, MODE_PRIME, L.Q, nxblk, stream) != cudaSuccess) return NMF_ECUDA;
   if (ks.ypass(p, MODE_SWEEP, L, stream) != cudaSuccess) return NMF_ECUDA;
   if (ks.xpass(p, MODE_SWEEP, L.Q, nxblk, stream) != cudaSuccess) return NMF_ECUDA;
-  if (cudaMemcpyAsync(X, Xn, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
-    return NMF_ECUDA;
-  if (cudaMemcpyAsync(Y, Yn, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
-    return NMF_ECUDA;
-  if (stats_dev &&
-      cudaMemcpyAsync(stats_dev, st->stats[0], sizeof(double) * NSTAT, cudaMemcpyDeviceToDevice,
-                      stream) != cudaSuccess)
-    return NMF_ECUDA;
+  na_finish_kernel<<<32, 256, 0, stream>>>(st, Xn, X, (long long)n * k, Yn, Y, (long long)m * k, stats_dev);
+  if (cudaGetLastError() != cudaSuccess) return NMF_ECUDA;
   return NMF_OK;
 }
