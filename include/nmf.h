@@ -70,13 +70,13 @@ enum { NMF_WARM_COLD = 0, NMF_WARM_PREV = 1 };
 typedef struct {
     int64_t n;               /* rows of M (distance grid)                     */
     int64_t m_capacity;      /* resident time columns (ring buffer capacity)  */
-    int32_t k;               /* rank, 1..8 or 16                              */
+    int32_t k;               /* rank, 1..8 or 16 (see nmf_create)             */
     int32_t prec;            /* nmf_precision                                 */
     double stol;             /* eps_STOL of the Sec. 4 relative step test;
                                 <= 0 disables                                 */
     double kkt_target;       /* stop when the relative KKT error <= target;
                                 <= 0 disables                                 */
-    double mixed_switch;     /* MIXED: move to FP64-accumulated passes once the
+    double mixed_switch;     /* MIXED: move to the refinement passes once the
                                 relative KKT error <= this (or stalls)       */
     int32_t max_sweeps;      /* cap for nmf_sweep(h, 0, ...)                  */
     int32_t warm_start;      /* NMF_WARM_COLD or NMF_WARM_PREV                */
@@ -87,7 +87,9 @@ typedef struct {
     int32_t sweeps;          /* sweeps run by this call                        */
     int32_t iter;            /* index of the current iterate                   */
     int32_t converged;       /* 1 rel-KKT target met, 2 step test met, 0 not   */
-    int32_t fp64_sweeps;     /* sweeps of this call whose M pass ran in FP64   */
+    int32_t fp64_sweeps;     /* sweeps of this call in the refinement phase:
+                                FP64-accurate contractions (FP64, compensated
+                                or incremental M pass)                        */
     double f;                /* 1/2 ||XY - M||^2 of the last measured iterate  */
     double kkt_abs;          /* E(x, y, r, s; 0) with r = max(graX,0),
                                 s = max(graY,0) (Sec. 5.1), 2-norms            */
@@ -110,6 +112,10 @@ void nmf_config_init(nmf_config *cfg);
  * nmf_append_columns' staging of host data.  Errors: NMF_EINVAL for n < 1,
  * k outside 1..8 and 16, m_capacity < 1 or n beyond the kernels' row limit
  * (16384 rows FP32, 8192 FP64); NMF_ENOMEM; NMF_ECUDA.
+ * Ranks: the passive-set masks would hold k <= 32, but the kernels are built
+ * for k = 1..8 (subset tables of inv(G_PP) for all 2^k passive sets, lanes of
+ * a warp per problem) and k = 16 (one 16-lane group per problem, the
+ * tensor-core contractions of the mixed form); other ranks are rejected.
  * Rank 16 with NMF_PREC_MIXED: the FP32-class pass runs on the tensor cores
  * (split-BF16 contractions, FP32 solves; about 1e-5 relative in B and P).
  * Where n is beyond the rows of the FP64-class kernels at rank 16 (n above
@@ -117,6 +123,10 @@ void nmf_config_init(nmf_config *cfg);
  * leaves it, pass modes 1 and 2 run it as well, and nmf_objective_kkt
  * measures with it. */
 nmf_status nmf_create(const nmf_config *cfg, nmf_handle **out);
+
+/* The configuration the handle was created with (its cuda_stream field is
+ * the stream the handle's work is ordered on).  NMF_EINVAL for NULL. */
+nmf_status nmf_get_config(const nmf_handle *h, nmf_config *out);
 
 /* Free every resource of the handle (NULL is accepted). */
 nmf_status nmf_destroy(nmf_handle *h);
@@ -157,8 +167,15 @@ nmf_status nmf_sweep(nmf_handle *h, int32_t nsweeps, nmf_stats *stats);
 /* NMF_PREC_MIXED handles: force the arithmetic of the following M passes
  * (0 = FP32 contraction, 1 = FP64-accumulated contraction of the FP32 M,
  * 2 = compensated FP32 (double-float) contraction of the FP32 M, about 44
- * significant bits; -1 = automatic: FP32 until the relative KKT error reaches
- * mixed_switch or stalls, then compensated).  NMF_PREC_FP64 handles ignore it.
+ * significant bits; 3 = incremental: every chunk of up to 32 sweeps starts
+ * with a compensated sweep that records its contractions B_ref = X_t^T M and
+ * P_ref = M Y_{t+1}^T as references, and its other sweeps form
+ * B = B_ref + (X - X_t)^T M and P = P_ref + M (Y - Y_{t+1})^T with the change
+ * terms contracted in FP32 -- their rounding is 2^-24 of the change, so
+ * near convergence the sweep is as accurate as the compensated one at the
+ * cost of an FP32 pass; -1 = automatic: FP32 until the relative KKT error
+ * reaches mixed_switch or stalls, then incremental (compensated where the
+ * incremental pass has no launch plan)).  NMF_PREC_FP64 handles ignore it.
  * At rank 16, mode 0 is the tensor-core pass (see nmf_create).
  * NMF_EINVAL for any other mode. */
 nmf_status nmf_set_pass_mode(nmf_handle *h, int32_t mode);
@@ -191,6 +208,27 @@ nmf_status nmf_set_timing(nmf_handle *h, int32_t on);
 nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launches,
                           double *xpass_ms, int64_t *xpass_launches);
 
+/* Persistence of a stream's state (the streaming setting of Sec. 1 keeps a
+ * problem resident for as long as its columns keep arriving; these calls let
+ * that state outlive the process).  nmf_save writes to the file at path: the
+ * configuration (without its stream), the resident window of M in logical
+ * column order, the current iterate X, Y with its passive sets and Gram G
+ * (and, k <= 8, G's subset table), the device control block (iterate index,
+ * statistics, KKT terms of the iterate, ||M||^2) and the mixed schedule's
+ * state.  It synchronises the handle's stream and leaves the handle as it
+ * was.  nmf_load creates a new handle on cuda_stream (NULL: the library
+ * creates one) holding that state, with the window in the ring's first
+ * columns; sweeps of the loaded handle give bitwise the results the saved
+ * handle would give (the sweep's partitions follow logical column order).
+ * The file is in the byte order of the machine that wrote it (little-endian
+ * on the x86-64 and Arm hosts this library builds for) and is specific to
+ * this library version: nmf_load rejects a file whose header, sizes or length
+ * do not match (NMF_EINVAL, before any device allocation).  Errors: NMF_EINVAL
+ * for NULL arguments or a path that cannot be opened, read or written; the
+ * errors of nmf_create; NMF_ECUDA. */
+nmf_status nmf_save(nmf_handle *h, const char *path);
+nmf_status nmf_load(const char *path, void *cuda_stream, nmf_handle **out);
+
 /* One ANLS sweep that allocates no memory at all.
  *
  * The paper has no counterpart: this is a deployment variant of nmf_sweep for
@@ -208,9 +246,17 @@ nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launch
  *              iterate (entries >= 0), on exit the next iterate: one sweep,
  *              Y-update then X-update, with the FP64-accumulated M pass;
  *   stats_dev  NULL or a device buffer of 16 doubles that receives the record of
- *              the incoming iterate (index 1: f, 2: KKT error, 3: relative KKT);
+ *              the incoming iterate (index 1: f, 2: KKT error, 3: relative KKT)
+ *              and, at index 15, the sweep's device error bits: 0 when the sweep
+ *              completed, bit 0 (1) when a bounded device wait gave up, bit 1 (2)
+ *              when a non-finite value was met.  With any bit set, X and Y are
+ *              left holding the incoming iterate.  Pass a record to learn of
+ *              these errors: the call returns before the device work runs;
  *   cuda_stream  the stream the work is ordered on (NULL: the default stream);
  *              the call returns once the work is enqueued.
+ * Alignment: M must be 16-byte aligned (the M pass stages column segments with
+ * bulk copies), X, Y and stats_dev 8-byte aligned; otherwise NMF_EINVAL, before
+ * any device work.
  * Limits: n <= 2048, m <= 4096, 1 <= k <= 8; larger sizes return NMF_ECAPACITY,
  * a wrong ldm or a NULL pointer NMF_EINVAL.
  * Working memory: one 5 MiB __device__ array compiled into the library, which
@@ -220,7 +266,12 @@ nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launch
  * streams or from different threads -- race on it; serialise them.
  * Set-up: the first call on each device looks up the array's device address
  * with that device current; make that first call before any stream capture
- * on the device. */
+ * on the device.  With CUDA's lazy module loading (the default), that first
+ * call is also when the driver loads the library's kernels and places the
+ * array in device memory -- an allocation by the driver -- so make it at
+ * start-up, while device memory is still free, or set
+ * CUDA_MODULE_LOADING=EAGER so that the array is placed when the CUDA context
+ * is created. */
 nmf_status nmf_sweep_noalloc(const float *M, int64_t n, int64_t m, int64_t ldm, int32_t k,
                              double *X, double *Y, double *stats_dev, void *cuda_stream);
 

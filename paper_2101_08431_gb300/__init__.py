@@ -131,6 +131,24 @@ class StreamingNMF:
     def launches(self):
         return int(self.lib.nmf_launch_count(self.h))
 
+    # -- persistence ------------------------------------------------------------
+    def save(self, path):
+        """Write the handle's window, iterate and sweep state to path."""
+        check(self.lib.nmf_save(self.h, str(path).encode()), self.h)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A new handle holding the state saved at path (on `stream`)."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        h = C.c_void_p()
+        check(self.lib.nmf_load(str(path).encode(), stream, C.byref(h)))
+        self.h = h
+        cfg = nmf_config()
+        check(self.lib.nmf_get_config(h, C.byref(cfg)), h)
+        self.n, self.k, self.m_capacity = int(cfg.n), int(cfg.k), int(cfg.m_capacity)
+        return self
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.nmf_destroy(self.h)

@@ -1,6 +1,7 @@
 // C ABI of the GB300 streaming-NMF library (declared in include/nmf.h):
 // handle life cycle, the resident column ring, priming, the sweep driver with
 // the mixed-precision schedule, and the read-only objective / KKT pass.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -164,6 +165,13 @@ struct nmf_handle {
   unsigned* dNonfinite = nullptr;
   void* dStage = nullptr;
   size_t stage_bytes = 0;
+  // references and FP32 change of X for the incremental refinement sweeps
+  double* dBref = nullptr;
+  double* dYref = nullptr;
+  double* dPref = nullptr;
+  double* dXref = nullptr;
+  float* dXd32[2] = {nullptr, nullptr};
+  bool inc_ok = false;            // the incremental pass has a plan for this shape
   DevState* hSt = nullptr;      // pinned mirror
   double* hKkt = nullptr;
   unsigned* hNonfinite = nullptr;
@@ -178,7 +186,7 @@ struct nmf_handle {
   int64_t launches = 0;
   std::string last_error;
   KernelSet ks[NVAR]{};
-  bool has[NVAR] = {false, false, false, false};
+  bool has[NVAR] = {};
   int max_clusters[NVAR][4] = {};   // per variant, cluster size 1, 2, 4, 8 (full smem)
   // CUDA graph of one chunk of sweeps per variant, keyed by the ring state
   // it was captured with (m, head); a signature is first run uncaptured
@@ -285,6 +293,14 @@ Problem make_problem(const nmf_handle* h, int var) {
   p.Yterms = h->dYterms;
   p.Xpart = h->dXpart;
   p.st = h->dSt;
+  p.Bref = h->dBref;
+  p.Yref = h->dYref;
+  p.Pref = h->dPref;
+  p.Xref = h->dXref;
+  p.Xd32[0] = h->dXd32[0];
+  p.Xd32[1] = h->dXd32[1];
+  p.inc = var == VAR_INC ? 1 : 0;
+  p.record_refs = 0;
   p.warm = h->cfg.warm_start != NMF_WARM_COLD;
   p.fp64_pass = var != VAR_F32;
   const bool final_phase = !(h->store_f32 && var == VAR_F32);
@@ -309,8 +325,9 @@ nmf_status drain_timing(nmf_handle* h) {
   return NMF_OK;
 }
 
-// One sweep (M pass + row pass) or, with mode PRIME, the priming pair.
-nmf_status launch_pair(nmf_handle* h, int var, int mode) {
+// One sweep (M pass + row pass) or, with mode PRIME, the priming pair;
+// record: this (compensated) sweep records the incremental references.
+nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
   YPlan L{};
   Tc16Plan T{};
   const bool use_tc = h->tc16 && var == VAR_F32;
@@ -326,6 +343,7 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode) {
     return fail(h, NMF_EINVAL, "no launch plan for this shape");
   }
   Problem p = make_problem(h, var);
+  p.record_refs = record ? 1 : 0;
   const bool timed = h->timing && mode == MODE_SWEEP;
   if (timed && h->nev == nmf_handle::NEV) {
     nmf_status s = drain_timing(h);
@@ -348,11 +366,25 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode) {
   return NMF_OK;
 }
 
-// CHUNK sweeps of variant var: replay of the captured graph when its
-// signature matches, otherwise plain launches (captured the second time the
-// same signature is seen).
-nmf_status launch_chunk(nmf_handle* h, int var, int chunk) {
-  nmf_handle::ChunkGraph& g = h->graphs[var];
+// The passes of one chunk of sweeps: `first` for its first sweep (which
+// records the incremental references when `record`), `rest` for the others.
+struct ChunkPlan {
+  int first, rest;
+  bool record;
+};
+
+// CHUNK sweeps of a plan: replay of the captured graph when its signature
+// matches, otherwise plain launches (captured the second time the same
+// signature is seen).  Graphs are kept per plan (indexed by `rest`).
+nmf_status launch_chunk(nmf_handle* h, const ChunkPlan& cp, int chunk) {
+  nmf_handle::ChunkGraph& g = h->graphs[cp.rest];
+  auto launch_all = [&]() -> nmf_status {
+    for (int i = 0; i < chunk; ++i) {
+      nmf_status s = launch_pair(h, i == 0 ? cp.first : cp.rest, MODE_SWEEP, i == 0 && cp.record);
+      if (s != NMF_OK) return s;
+    }
+    return NMF_OK;
+  };
   const bool graphable = !h->timing && chunk == CHUNK;
   if (graphable && g.exec && g.m == h->m && g.head == h->head) {
     CUDA_TRY(h, cudaGraphLaunch(g.exec, h->stream));
@@ -364,9 +396,8 @@ nmf_status launch_chunk(nmf_handle* h, int var, int chunk) {
     g.exec = nullptr;
     cudaGraph_t graph = nullptr;
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    nmf_status s = NMF_OK;
     const int64_t l0 = h->launches;
-    for (int i = 0; i < chunk && s == NMF_OK; ++i) s = launch_pair(h, var, MODE_SWEEP);
+    nmf_status s = launch_all();
     h->launches = l0;
     const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (s != NMF_OK) {
@@ -383,10 +414,8 @@ nmf_status launch_chunk(nmf_handle* h, int var, int chunk) {
     h->launches += 2 * chunk;
     return NMF_OK;
   }
-  for (int i = 0; i < chunk; ++i) {
-    nmf_status s = launch_pair(h, var, MODE_SWEEP);
-    if (s != NMF_OK) return s;
-  }
+  nmf_status s = launch_all();
+  if (s != NMF_OK) return s;
   if (graphable) {
     g.seen_m = h->m;
     g.seen_head = h->head;
@@ -394,13 +423,21 @@ nmf_status launch_chunk(nmf_handle* h, int var, int chunk) {
   return NMF_OK;
 }
 
-int variant_for(const nmf_handle* h) {
-  if (!h->store_f32) return VAR_F64;
-  if (!h->refine_ok) return VAR_F32;
-  if (h->forced_mode == 0) return VAR_F32;
-  if (h->forced_mode == 1) return VAR_REF;
-  if (h->forced_mode == 2) return VAR_DF;
-  return h->phase ? VAR_DF : VAR_F32;
+// Passes of the next chunk.  The refinement phase of the mixed form, where
+// the incremental pass has a plan: a compensated sweep that records the
+// references, then incremental sweeps; otherwise compensated sweeps.
+ChunkPlan plan_for(const nmf_handle* h) {
+  auto one = [](int v) { return ChunkPlan{v, v, false}; };
+  if (!h->store_f32) return one(VAR_F64);
+  if (!h->refine_ok) return one(VAR_F32);
+  const ChunkPlan incremental = h->inc_ok ? ChunkPlan{VAR_DF, VAR_INC, true} : one(VAR_DF);
+  switch (h->forced_mode) {
+    case 0: return one(VAR_F32);
+    case 1: return one(VAR_REF);
+    case 2: return one(VAR_DF);
+    case 3: return incremental;
+    default: return h->phase ? incremental : one(VAR_F32);
+  }
 }
 
 nmf_status read_state(nmf_handle* h) {
@@ -475,6 +512,13 @@ int64_t nmf_launch_count(const nmf_handle* h) { return h ? h->launches : 0; }
 
 int64_t nmf_num_columns(const nmf_handle* h) { return h ? h->m : 0; }
 
+nmf_status nmf_get_config(const nmf_handle* h, nmf_config* out) {
+  if (!h || !out) return NMF_EINVAL;
+  *out = h->cfg;
+  out->cuda_stream = h->stream;
+  return NMF_OK;
+}
+
 nmf_status nmf_destroy(nmf_handle* h) {
   if (!h) return NMF_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -486,7 +530,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
   void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dX32lo[0], h->dX32lo[1], h->dY[0], h->dY[1],
                    h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dHg, h->dHtab, h->dHok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
-                   h->dNonfinite, h->dStage};
+                   h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1]};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->hSt) cudaFreeHost(h->hSt);
@@ -526,6 +570,7 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   h->has[VAR_REF] = get_kernels_ref(k, &h->ks[VAR_REF]);
   h->has[VAR_F64] = get_kernels_f64(k, &h->ks[VAR_F64]);
   h->has[VAR_DF] = get_kernels_df(k, &h->ks[VAR_DF]);
+  h->has[VAR_INC] = get_kernels_inc(k, &h->ks[VAR_INC]);
   for (int v = 0; v < NVAR; ++v)
     if (h->has[v])
       for (int ci = 0; ci < 4; ++ci)
@@ -551,6 +596,13 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
       }
       if (!ok) return bail(NMF_EINVAL, "n too large for the kernels of this precision");
     }
+    if (h->store_f32 && h->refine_ok && h->has[VAR_INC]) {
+      YPlan L;
+      int msave = h->m;
+      h->m = h->mcap;
+      h->inc_ok = make_plan(h, VAR_INC, &L);
+      h->m = msave;
+    }
   }
   if (cfg->cuda_stream) {
     h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
@@ -572,6 +624,14 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
     ok &= dalloc(&h->dXm[b], h->n) == cudaSuccess;
   }
   ok &= dalloc(&h->dG, (size_t)k * k) == cudaSuccess;
+  if (h->inc_ok) {
+    ok &= dalloc(&h->dBref, mk) == cudaSuccess;
+    ok &= dalloc(&h->dYref, mk) == cudaSuccess;
+    ok &= dalloc(&h->dPref, nk) == cudaSuccess;
+    ok &= dalloc(&h->dXref, nk) == cudaSuccess;
+    ok &= dalloc(&h->dXd32[0], nk) == cudaSuccess;
+    ok &= dalloc(&h->dXd32[1], nk) == cudaSuccess;
+  }
   if (k <= 8) {
     ok &= dalloc(&h->dGtab, ((size_t)1 << k) * k * k) == cudaSuccess;
     ok &= dalloc(&h->dGok, (size_t)1 << k) == cudaSuccess;
@@ -774,7 +834,7 @@ nmf_status nmf_get_timing(nmf_handle* h, double* ypass_ms, int64_t* ypass_launch
 }
 
 nmf_status nmf_set_pass_mode(nmf_handle* h, int32_t mode) {
-  if (!h || mode < -1 || mode > 2) return NMF_EINVAL;
+  if (!h || mode < -1 || mode > 3) return NMF_EINVAL;
   h->forced_mode = mode;
   return NMF_OK;
 }
@@ -797,13 +857,18 @@ nmf_status nmf_sweep(nmf_handle* h, int32_t nsweeps, nmf_stats* stats) {
   int launched = 0, worked = 0, fp64_sweeps = 0, measured = -1;
   bool done = false;
   while (launched < cap) {
-    const int chunk = need_checks ? std::min(CHUNK, cap - launched) : cap - launched;
-    const int var = variant_for(h);
-    s = launch_chunk(h, var, chunk);
+    const ChunkPlan cp = plan_for(h);
+    // chunks of incremental sweeps never exceed CHUNK: each starts from the
+    // references its first sweep records
+    const bool split = need_checks || cp.first != cp.rest;
+    const int chunk = split ? std::min(CHUNK, cap - launched) : cap - launched;
+    const int var = cp.rest;
+    s = launch_chunk(h, cp, chunk);
     if (s != NMF_OK) return s;
     launched += chunk;
     if (!need_checks) {
       h->snap_valid = false;
+      if (launched < cap) continue;
       break;
     }
     s = read_state(h);
@@ -876,6 +941,213 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
   return NMF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// persistence: the resident window, the iterate and the sweep state
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char SAVE_MAGIC[8] = {'N', 'M', 'F', 'G', 'B', '3', '0', '0'};
+constexpr uint32_t SAVE_VERSION = 1;
+
+struct SaveHeader {
+  char magic[8];
+  uint32_t version, devstate_bytes;
+  int64_t n, ld, mcap, m;
+  int32_t k, prec, max_sweeps, warm_start;
+  double stol, kkt_target, mixed_switch;
+  int32_t factors_set, phase, forced_mode, chunks_since_best;
+  double best_rel;
+};
+
+// copy the logical columns [0, m) of a ring of `width` elements per column
+// (physical column of logical j: (head + j) mod mcap) between device and host
+cudaError_t ring_copy(void* host, void* dev, size_t width_bytes, int head, int m, int mcap, bool to_host,
+                      cudaStream_t s) {
+  const int first = std::min(m, mcap - head);
+  char* hp = static_cast<char*>(host);
+  char* dp = static_cast<char*>(dev);
+  const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaSuccess;
+  if (first > 0) {
+    e = to_host ? cudaMemcpyAsync(hp, dp + (size_t)head * width_bytes, (size_t)first * width_bytes, kind, s)
+                : cudaMemcpyAsync(dp + (size_t)head * width_bytes, hp, (size_t)first * width_bytes, kind, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (first < m)
+    e = to_host ? cudaMemcpyAsync(hp + (size_t)first * width_bytes, dp, (size_t)(m - first) * width_bytes, kind, s)
+                : cudaMemcpyAsync(dp, hp + (size_t)first * width_bytes, (size_t)(m - first) * width_bytes, kind, s);
+  return e;
+}
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+
+}  // namespace
+
+nmf_status nmf_save(nmf_handle* h, const char* path) {
+  if (!h || !path) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  nmf_status s = read_state(h);
+  if (s != NMF_OK && s != NMF_ENUMERIC) return s;
+  SaveHeader hd{};
+  std::memcpy(hd.magic, SAVE_MAGIC, 8);
+  hd.version = SAVE_VERSION;
+  hd.devstate_bytes = (uint32_t)sizeof(DevState);
+  hd.n = h->n;
+  hd.ld = h->ld;
+  hd.mcap = h->mcap;
+  hd.m = h->m;
+  hd.k = h->k;
+  hd.prec = h->cfg.prec;
+  hd.max_sweeps = h->cfg.max_sweeps;
+  hd.warm_start = h->cfg.warm_start;
+  hd.stol = h->cfg.stol;
+  hd.kkt_target = h->cfg.kkt_target;
+  hd.mixed_switch = h->cfg.mixed_switch;
+  hd.factors_set = h->factors_set ? 1 : 0;
+  hd.phase = h->phase;
+  hd.forced_mode = h->forced_mode;
+  hd.chunks_since_best = h->chunks_since_best;
+  hd.best_rel = h->best_rel;
+  const int cur = h->hSt->iter & 1;
+  const size_t k = h->k, esz = h->store_f32 ? 4 : 8, nk = (size_t)h->n * k;
+  std::string buf;
+  const size_t mbytes = (size_t)h->ld * h->m * esz;
+  const size_t tab = k <= 8 ? ((size_t)1 << k) : 0;
+  buf.resize(mbytes + h->m * 8 + h->m * k * 8 + h->m * 4 + nk * (8 + 4 + 4) + h->n * 4 + k * k * 8 +
+             tab * k * k * 8 + tab * 4);
+  char* p = &buf[0];
+  char* const pm = p;                 p += mbytes;
+  char* const pcol = p;               p += (size_t)h->m * 8;
+  char* const py = p;                 p += (size_t)h->m * k * 8;
+  char* const pym = p;                p += (size_t)h->m * 4;
+  char* const px = p;                 p += nk * 8;
+  char* const px32 = p;               p += nk * 4;
+  char* const px32lo = p;             p += nk * 4;
+  char* const pxm = p;                p += (size_t)h->n * 4;
+  char* const pg = p;                 p += k * k * 8;
+  char* const ptab = p;               p += tab * k * k * 8;
+  char* const pok = p;
+  cudaStream_t st = h->stream;
+  CUDA_TRY(h, ring_copy(pm, h->dM, (size_t)h->ld * esz, h->head, h->m, h->mcap, true, st));
+  CUDA_TRY(h, ring_copy(pcol, h->dColsq, 8, h->head, h->m, h->mcap, true, st));
+  CUDA_TRY(h, ring_copy(py, h->dY[cur], k * 8, h->head, h->m, h->mcap, true, st));
+  CUDA_TRY(h, ring_copy(pym, h->dYm[cur], 4, h->head, h->m, h->mcap, true, st));
+  CUDA_TRY(h, cudaMemcpyAsync(px, h->dX[cur], nk * 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(px32, h->dX32[cur], nk * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(px32lo, h->dX32lo[cur], nk * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(pxm, h->dXm[cur], (size_t)h->n * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(pg, h->dG, k * k * 8, cudaMemcpyDeviceToHost, st));
+  if (tab) {
+    CUDA_TRY(h, cudaMemcpyAsync(ptab, h->dGtab, tab * k * k * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaMemcpyAsync(pok, h->dGok, tab * 4, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  FileCloser fc{std::fopen(path, "wb")};
+  if (!fc.f) return fail(h, NMF_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, fc.f) == 1;
+  ok = ok && std::fwrite(h->hSt, sizeof(DevState), 1, fc.f) == 1;
+  ok = ok && std::fwrite(buf.data(), 1, buf.size(), fc.f) == buf.size();
+  ok = (std::fclose(fc.f) == 0) && ok;
+  fc.f = nullptr;
+  if (!ok) return fail(h, NMF_EINVAL, std::string("write to ") + path + " failed");
+  return NMF_OK;
+}
+
+nmf_status nmf_load(const char* path, void* cuda_stream, nmf_handle** out) {
+  if (!path || !out) return NMF_EINVAL;
+  *out = nullptr;
+  FileCloser fc{std::fopen(path, "rb")};
+  if (!fc.f) return NMF_EINVAL;
+  SaveHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, fc.f) != 1) return NMF_EINVAL;
+  if (std::memcmp(hd.magic, SAVE_MAGIC, 8) != 0 || hd.version != SAVE_VERSION ||
+      hd.devstate_bytes != (uint32_t)sizeof(DevState))
+    return NMF_EINVAL;
+  if (hd.n < 1 || hd.n > (1 << 20) || hd.ld != (int64_t)round_up((int)hd.n, 32) || hd.mcap < 1 ||
+      hd.mcap > (1 << 24) || hd.m < 0 || hd.m > hd.mcap || !((hd.k >= 1 && hd.k <= 8) || hd.k == 16) ||
+      (hd.prec != NMF_PREC_FP64 && hd.prec != NMF_PREC_MIXED) || hd.forced_mode < -1 || hd.forced_mode > 2 ||
+      (hd.factors_set && hd.m < 1))
+    return NMF_EINVAL;
+  DevState ds;
+  if (std::fread(&ds, sizeof(ds), 1, fc.f) != 1) return NMF_EINVAL;
+  const size_t k = hd.k, m = hd.m, n = hd.n, nk = n * k, esz = hd.prec == NMF_PREC_MIXED ? 4 : 8;
+  const size_t tab = k <= 8 ? ((size_t)1 << k) : 0;
+  const size_t total = (size_t)hd.ld * m * esz + m * 8 + m * k * 8 + m * 4 + nk * 16 + n * 4 + k * k * 8 +
+                       tab * k * k * 8 + tab * 4;
+  std::string buf(total, '\0');
+  if (std::fread(&buf[0], 1, total, fc.f) != total) return NMF_EINVAL;
+  char extra;
+  if (std::fread(&extra, 1, 1, fc.f) != 0) return NMF_EINVAL;     // trailing bytes: not this format
+  nmf_config cfg;
+  nmf_config_init(&cfg);
+  cfg.n = hd.n;
+  cfg.m_capacity = hd.mcap;
+  cfg.k = hd.k;
+  cfg.prec = hd.prec;
+  cfg.stol = hd.stol;
+  cfg.kkt_target = hd.kkt_target;
+  cfg.mixed_switch = hd.mixed_switch;
+  cfg.max_sweeps = hd.max_sweeps;
+  cfg.warm_start = hd.warm_start;
+  cfg.cuda_stream = cuda_stream;
+  nmf_handle* h = nullptr;
+  nmf_status s = nmf_create(&cfg, &h);
+  if (s != NMF_OK) return s;
+  auto bail = [&](nmf_status e) {
+    nmf_destroy(h);
+    return e;
+  };
+  const char* p = buf.data();
+  const char* pm = p;      p += (size_t)hd.ld * m * esz;
+  const char* pcol = p;    p += m * 8;
+  const char* py = p;      p += m * k * 8;
+  const char* pym = p;     p += m * 4;
+  const char* px = p;      p += nk * 8;
+  const char* px32 = p;    p += nk * 4;
+  const char* px32lo = p;  p += nk * 4;
+  const char* pxm = p;     p += n * 4;
+  const char* pg = p;      p += k * k * 8;
+  const char* ptab = p;    p += tab * k * k * 8;
+  const char* pok = p;
+  const int cur = ds.iter & 1;
+  cudaStream_t st = h->stream;
+  // the window lands in physical columns 0 .. m-1 (head 0); every partition
+  // of the sweep follows logical column order, so results do not depend on it
+  bool ok = cudaMemcpyAsync(h->dM, pm, (size_t)hd.ld * m * esz, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dColsq, pcol, m * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dY[cur], py, m * k * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dYm[cur], pym, m * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dX[cur], px, nk * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dX32[cur], px32, nk * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dX32lo[cur], px32lo, nk * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dXm[cur], pxm, n * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->dG, pg, k * k * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (tab) {
+    ok = ok && cudaMemcpyAsync(h->dGtab, ptab, tab * k * k * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(h->dGok, pok, tab * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  }
+  ds.done = 0;
+  ds.xblocks_done = 0;
+  ok = ok && cudaMemcpyAsync(h->dSt, &ds, sizeof(ds), cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) return bail(NMF_ECUDA);
+  h->m = (int)m;
+  h->head = 0;
+  h->factors_set = hd.factors_set != 0;
+  h->phase = hd.phase;
+  h->forced_mode = hd.forced_mode;
+  h->chunks_since_best = hd.chunks_since_best;
+  h->best_rel = hd.best_rel;
+  h->snap_valid = false;
+  *out = h;
+  return NMF_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -893,6 +1165,7 @@ int64_t handle_footprint(int64_t n, int k, int64_t mcap, bool store_f32, int nsm
   b += (int64_t)nsm * (ld * k * 8 + k * k * 8 + NYT * 8);            // cluster partials
   b += nxblk * (k * k + NXT) * 8 + (int64_t)sizeof(DevState) + 4096;
   b += (int64_t)APPEND_STAGE_COLS * ld * 8;                          // append staging
+  if (store_f32) b += 2 * mk * 8 + 2 * nk * 8 + 2 * nk * 4;           // incremental references
   return b;
 }
 

@@ -3,6 +3,10 @@
 //   ArF32 : FP32 operands, FP32 FMA accumulation (bulk sweeps of the mixed form)
 //   ArF64 : FP64 operands and accumulation (the FP64 form, and the plain
 //           FP64-accumulated refinement of FP32 M)
+//   ArInc : incremental contraction for the refinement sweeps of the mixed
+//           form: FP32 operands and FP32 accumulation like ArF32, but of the
+//           change of X (and of Y) since the last compensated sweep, whose
+//           contractions are added back in FP64 (Problem::Bref, Pref)
 //   ArDF  : compensated FP32 ("double-float") accumulation of FP32 M times
 //           FP64 factors, for the refinement sweeps of the mixed form.  A
 //           factor value x is carried as hi + lo with hi = fl32(x),
@@ -19,8 +23,8 @@
 // B: FP32 instructions only where the pass itself avoids FP64), load_x /
 // yval (staging of X from its stored copies, of y from FP64), zero, vzero,
 // madd, add, shfl_xor, to_double, to_p, to_r, radd, rshfl_xor, r_to_double,
-// and EPS (the epsilon of the NNLS entering tolerance for sweeps computed
-// with this policy).
+// EPS (the epsilon of the NNLS entering tolerance for sweeps computed with
+// this policy) and INC (the incremental form).
 #pragma once
 
 #include "nmf_common.cuh"
@@ -79,8 +83,12 @@ struct ArF32 {
   using A = float;
   using P = float;
   static constexpr bool XD = false;   // X is staged from its FP32 copy
+  static constexpr bool INC = false;
   static constexpr bool PACC_SMEM = false;   // P accumulators in registers
-  static constexpr double EPS = 1.1920928955078125e-07;
+  // the FP64 column solves take the FP64 entering tolerance: a coarser one
+  // leaves out variables whose small gradient hides a large value where G is
+  // ill conditioned
+  static constexpr double EPS = 2.220446049250313e-16;
   using R = DF;   // cross-warp / cross-CTA reduction of B
   __device__ static V load_x(const Problem& p, int b, size_t i) { return p.X32[b][i]; }
   __device__ static V vzero() { return 0.f; }
@@ -103,6 +111,7 @@ struct ArF64 {
   using A = double;
   using P = double;
   static constexpr bool XD = true;
+  static constexpr bool INC = false;
   static constexpr bool PACC_SMEM = false;
   static constexpr double EPS = 2.220446049250313e-16;
   using R = double;
@@ -127,6 +136,7 @@ struct ArDF {
   using A = DF;
   using P = DF;   // partials stay double-float: no FP64 instruction in the epilogue
   static constexpr bool XD = true;
+  static constexpr bool INC = false;
   static constexpr double EPS = 5.684341886080802e-14;   // 2^-44
   // the P accumulators (two words each) live in shared memory, so that a
   // CTA holds as many rows as in the FP32 pass (no cluster exchange)
@@ -157,6 +167,33 @@ struct ArDF {
   __device__ static A add(A a, A b) { return df_add(a, b); }
   __device__ static A shfl_xor(A a, int o) { return df_shfl_xor(a, o); }
   __device__ static double to_double(A a) { return (double)a.hi + (double)a.lo; }
+  __device__ static P to_p(A a) { return a; }
+};
+
+struct ArInc {
+  using V = float;
+  using A = float;
+  using P = float;     // partials of M (Y - Yref)^T
+  // FP64-class solves (one refinement step): B and P are FP64-accurate
+  static constexpr bool XD = true;
+  static constexpr bool INC = true;
+  static constexpr bool PACC_SMEM = false;
+  static constexpr double EPS = 5.684341886080802e-14;   // 2^-44, as the compensated pass
+  using R = DF;
+  // the row pass that produced X wrote fl32(X - Xref)
+  __device__ static V load_x(const Problem& p, int b, size_t i) { return p.Xd32[b][i]; }
+  __device__ static V vzero() { return 0.f; }
+  __device__ static R to_r(A a) { return {a, 0.f}; }
+  __device__ static R radd(R a, R b) { return df_add(a, b); }
+  __device__ static R rshfl_xor(R a, int o) { return df_shfl_xor(a, o); }
+  __device__ static double r_to_double(R a) { return (double)a.hi + (double)a.lo; }
+  __device__ static V yval(double dy) { return (float)dy; }   // called with y - yref
+  __device__ static A zero() { return 0.f; }
+  template <typename TM>
+  __device__ static A madd(TM m, V v, A a) { return __fmaf_rn((float)m, v, a); }
+  __device__ static A add(A a, A b) { return __fadd_rn(a, b); }
+  __device__ static A shfl_xor(A a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static double to_double(A a) { return (double)a; }
   __device__ static P to_p(A a) { return a; }
 };
 

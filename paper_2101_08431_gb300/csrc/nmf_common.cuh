@@ -62,7 +62,9 @@ enum Variant {
   VAR_REF = 1,   // FP32 M, FP64 contraction (mixed precision, refinement sweeps)
   VAR_F64 = 2,   // FP64 M, FP64 contraction (the plain FP64 form)
   VAR_DF = 3,    // FP32 M, compensated FP32 contraction (mixed precision, refinement sweeps)
-  NVAR = 4
+  VAR_INC = 4,   // FP32 M, incremental contraction: references from the last compensated
+                 // sweep plus the FP32 contraction of the change of X and Y since it
+  NVAR = 5
 };
 
 // One problem as the kernels see it.
@@ -102,6 +104,21 @@ struct Problem {
   int auto_mixed;
   int stall_sweeps;
   double mixed_switch;
+  // incremental contractions (VAR_INC) of the mixed form.  A compensated sweep
+  // with record_refs = 1 stores its exact-to-~44-bit contractions as
+  // references: Bref_j = X_t^T M_{:,j} with Xref = X_t, and Pref = M Y_{t+1}^T
+  // with Yref = Y_{t+1}.  An incremental sweep (inc = 1) forms
+  // B_j = Bref_j + (X - Xref)^T M_{:,j} and P = Pref + M (Y - Yref)^T, the
+  // change terms contracted in FP32: their rounding is 2^-24 of the change,
+  // not of the contraction.  Every row pass of either kind writes
+  // Xd32 = fl32(X_{t+1} - Xref) for the next incremental sweep.
+  double* Bref;           // k x mcap (physical column order)
+  double* Yref;           // k x mcap (physical column order)
+  double* Pref;           // n x k row-major
+  double* Xref;           // n x k row-major
+  float* Xd32[2];         // n x k row-major, by iterate parity
+  int inc;                // 1: this sweep is incremental
+  int record_refs;        // 1: this (compensated) sweep records the references
 };
 
 enum Mode { MODE_SWEEP = 0, MODE_PRIME = 1, MODE_KKT = 2 };

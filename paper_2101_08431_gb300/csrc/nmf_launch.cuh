@@ -25,6 +25,7 @@ bool get_kernels_f32(int k, KernelSet* out);
 bool get_kernels_ref(int k, KernelSet* out);
 bool get_kernels_f64(int k, KernelSet* out);
 bool get_kernels_df(int k, KernelSet* out);
+bool get_kernels_inc(int k, KernelSet* out);
 
 template <typename TM, typename AR, int K>
 cudaError_t launch_y(const Problem& p, int mode, const YPlan& L, cudaStream_t s) {

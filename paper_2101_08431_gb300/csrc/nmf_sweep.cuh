@@ -42,9 +42,10 @@ struct YTraits {
   static constexpr int VP = (V <= 1) ? 1 : (V <= 2) ? 2 : (V <= 4) ? 4 : (V <= 8) ? 8 : (V <= 16) ? 16 : 32;
   static_assert(V <= 32, "B tile must fit one warp reduce-scatter");
   static constexpr int ROWS = RPT * TC;                        // rows per CTA at most
-  // value type of the column solves: FP32 for the FP32 pass (its B is
-  // FP32-accurate), FP64 otherwise
-  static constexpr bool F32NN = !AR::XD && K <= 8;
+  // value type of the column solves: FP64 in every pass.  (An FP32 solve
+  // from an FP32 subset table carries about 2^-24 cond(G_PP), which exceeds
+  // the FP32 contraction's own error wherever G is not well conditioned.)
+  static constexpr bool F32NN = false;
   using NV = typename std::conditional<F32NN, float, double>::type;
   // the NNLS warp builds the table in shared memory: FP32 solves (k <= 8),
   // FP64 solves at k <= 6 (k = 7, 8: the FP64 table built by the row pass)
@@ -386,12 +387,18 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         gok = gglob ? p.Gok : sm.gok;
       }
       // warm start and passive set of the next tile, fetched one tile ahead
-      double yo_nx = 0.0;
+      // (incremental sweeps: with the column's reference contraction and y)
+      constexpr bool INC = AR::INC;
+      double yo_nx = 0.0, br_nx = 0.0, yr_nx = 0.0;
       uint32_t om_nx = 0;
       int ph_nx = 0;
       if (jj < min(TJ, ncols)) {
         ph_nx = wrap_col(p.head, c0 + jj, p.mcap);
         if (ca) yo_nx = p.Y[cur][(size_t)ph_nx * K + g.a];
+        if (INC && ca && mode == MODE_SWEEP) {
+          br_nx = p.Bref[(size_t)ph_nx * K + g.a];
+          yr_nx = p.Yref[(size_t)ph_nx * K + g.a];
+        }
         om_nx = p.ymask[cur][ph_nx];
       }
       if constexpr (Tr::LOCAL_TAB) {
@@ -408,19 +415,24 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         const int tj = min(TJ, ncols - t * TJ);
         const bool active = jj < tj;
         const bool comp = active && ca;
-        const double yo = yo_nx;
+        const double yo = yo_nx, bref = br_nx, yref = yr_nx;
         const uint32_t old_mask = om_nx;
         const int phys = ph_nx;
-        yo_nx = 0.0;
+        yo_nx = br_nx = yr_nx = 0.0;
         om_nx = 0;
         ph_nx = 0;
         if (t + 1 < ntiles && jj < min(TJ, ncols - (t + 1) * TJ)) {
           ph_nx = wrap_col(p.head, c0 + (t + 1) * TJ + jj, p.mcap);
           if (ca) yo_nx = p.Y[cur][(size_t)ph_nx * K + g.a];
+          if (INC && ca && mode == MODE_SWEEP) {
+            br_nx = p.Bref[(size_t)ph_nx * K + g.a];
+            yr_nx = p.Yref[(size_t)ph_nx * K + g.a];
+          }
           om_nx = p.ymask[cur][ph_nx];
         }
         if (!mbar_wait(&sm.bready[slot], (uint32_t)((t >> 1) & 1))) timed_out = true;
-        const double b = comp ? sm.Bfull[slot][jj * K + g.a] : 0.0;
+        // incremental sweeps: B = Bref + (X - Xref)^T m_j
+        const double b = comp ? (INC ? bref + sm.Bfull[slot][jj * K + g.a] : sm.Bfull[slot][jj * K + g.a]) : 0.0;
         if (mode != MODE_PRIME) {
           // Y-half KKT terms of the incoming iterate: g = G y - b (component a)
           double gy = -b;
@@ -477,6 +489,10 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
           if (crank == 0 && active) {
             if (ca) p.Y[nxt][(size_t)phys * K + g.a] = yn;
             if (g.a == 0) p.ymask[nxt][phys] = msk;
+            if (p.record_refs && ca) {   // references for the incremental sweeps
+              p.Bref[(size_t)phys * K + g.a] = b;
+              p.Yref[(size_t)phys * K + g.a] = yn;
+            }
           }
         } else {
           const uint32_t msk = g.bits(comp && dpos(yo));
@@ -489,7 +505,8 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         }
         if (jj < TJ && ca) {
           sm.ybufD[slot][jj][g.a] = active ? yn : 0.0;
-          sm.ybufA[slot][jj][g.a] = AR::yval(active ? yn : 0.0);
+          // incremental sweeps accumulate M (Y - Yref)^T
+          sm.ybufA[slot][jj][g.a] = AR::yval(active ? (INC && mode == MODE_SWEEP ? yn - yref : yn) : 0.0);
         }
         if (t == ntiles - 1) {
           // H over the column slots (fixed butterfly order), into Hacc
@@ -520,6 +537,8 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         double yo[K], yn[K];
         uint32_t old_mask = 0;
         int phys = 0;
+        constexpr bool INC = AR::INC;
+        const bool inc = INC && mode == MODE_SWEEP;
         if (lane < tj) {   // warm start and passive set, fetched before B is ready
           phys = wrap_col(p.head, c0 + t * TJ + lane, p.mcap);
 #pragma unroll
@@ -532,7 +551,8 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         if (lane < tj) {
           double b[K];
 #pragma unroll
-          for (int a = 0; a < K; ++a) b[a] = sm.Bfull[slot][lane * K + a];
+          for (int a = 0; a < K; ++a)
+            b[a] = sm.Bfull[slot][lane * K + a] + (inc ? p.Bref[(size_t)phys * K + a] : 0.0);
           double* yt = sm.yt[lane];
           if (mode != MODE_PRIME) {
             double neg = 0.0, comp = 0.0, bn = 0.0, by = 0.0, ygy = 0.0, ymax = 0.0, yn2 = 0.0;
@@ -572,6 +592,13 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
 #pragma unroll
               for (int a = 0; a < K; ++a) p.Y[nxt][(size_t)phys * K + a] = yn[a];
               p.ymask[nxt][phys] = msk;
+              if (p.record_refs) {
+#pragma unroll
+                for (int a = 0; a < K; ++a) {
+                  p.Bref[(size_t)phys * K + a] = b[a];
+                  p.Yref[(size_t)phys * K + a] = yn[a];
+                }
+              }
             }
           } else {
             uint32_t msk = 0;
@@ -587,7 +614,8 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
 #pragma unroll
           for (int a = 0; a < K; ++a) {
             sm.ybufD[slot][lane][a] = yn[a];
-            sm.ybufA[slot][lane][a] = AR::yval(yn[a]);
+            sm.ybufA[slot][lane][a] =
+                AR::yval((inc && lane < tj) ? yn[a] - p.Yref[(size_t)phys * K + a] : yn[a]);
           }
         }
         __syncwarp();
@@ -741,6 +769,21 @@ __device__ void tree_sum2(const double* src1, int np1, size_t st1, int n1, doubl
   }
 }
 
+// Row pass of an incremental sweep or of the compensated sweep that records
+// the references (entry e of row-major X): the FP32 change of the new X
+// against the reference X for the next incremental sweep; when recording,
+// the reference X (the sweep's input X, whose contractions the M pass just
+// recorded) and the reference P (this sweep's P, from the recorded Y).
+__device__ __forceinline__ void store_increment_refs(const Problem& p, int nxt, size_t e, double xo, double xn,
+                                                     double pr) {
+  const double xr = p.record_refs ? xo : p.Xref[e];
+  p.Xd32[nxt][e] = __double2float_rn(xn - xr);
+  if (p.record_refs) {
+    p.Xref[e] = xo;
+    p.Pref[e] = pr;
+  }
+}
+
 // Dynamic shared memory of the row pass: the working arrays, then the
 // subset table of H (k <= 8).
 template <typename TA, int K>
@@ -758,12 +801,14 @@ struct XSmem {
   }
   static constexpr int WT_NEED = (binom_mid() * LaneGroup<K>::KP + 31) / 32;
   static constexpr int WT = TABLE ? (WT_NEED < 1 ? 1 : (WT_NEED > Tr::NW / 2 ? Tr::NW / 2 : WT_NEED)) : 0;
-  // value type of the row solves: FP32 for the FP32 pass (P partials in
-  // FP32), FP64 otherwise
-  static constexpr bool F32NN = std::is_same<TA, float>::value && TABLE;
+  // value type of the row solves: FP64 in every pass (see YTraits::F32NN)
+  static constexpr bool F32NN = false;
   using SV = typename std::conditional<F32NN, float, double>::type;
-  // k = 16: value type of the 16-lane row solves (FP32 for the FP32 pass)
-  using V16 = typename std::conditional<std::is_same<TA, float>::value, float, double>::type;
+  // k = 16: value type of the 16-lane row solves
+  using V16 = double;
+  // Lawson-Hanson tolerance constant of the FP64 row solves (incremental
+  // sweeps use 2^-44, as the compensated pass)
+  static constexpr double EPS = 2.220446049250313e-16;
   struct Small {
     double H[K * K];
     double Gs[K * K];
@@ -898,6 +943,8 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
         TA ts = psum[0][lrow][g.a];
         for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][g.a]);
         pr = PartOps<TA>::to_double(ts);
+        // incremental sweeps: P = Pref + M (Y - Yref)^T
+        if (p.inc && mode == MODE_SWEEP) pr += p.Pref[(size_t)grow_i * K + g.a];
         xo = p.X[cur][(size_t)grow_i * K + g.a];
       }
       if (ract) old_mask = p.xmask[cur][grow_i];
@@ -907,7 +954,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       if (mode == MODE_SWEEP) {
         SV xnv = (SV)xn;
         stt = lane_table_nnls<K, SV>(g, tab, tok, hrown, (SV)solver.gmax,
-                                     F32NN ? (SV)1.1920928955078125e-07 : (SV)2.220446049250313e-16, (SV)pr,
+                                     (SV)(p.inc ? 5.684341886080802e-14 : Xs::EPS), (SV)pr,
                                      xnv, p.warm != 0, ract, true, &msk);
         xn = (double)xnv;
         if (__any_sync(0xffffffffu, stt < 0)) {
@@ -983,10 +1030,12 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       if (lane < 16) term_w[warp][lane] = (lane == XT_XMAX) ? mx : tr;
       if (mode == MODE_SWEEP) {
         if (comp) {
+          const size_t e = (size_t)grow_i * K + g.a;
           const float hi = __double2float_rn(xn);
-          p.X[nxt][(size_t)grow_i * K + g.a] = xn;
-          p.X32[nxt][(size_t)grow_i * K + g.a] = hi;
-          p.X32lo[nxt][(size_t)grow_i * K + g.a] = __double2float_rn(xn - (double)hi);
+          p.X[nxt][e] = xn;
+          p.X32[nxt][e] = hi;
+          p.X32lo[nxt][e] = __double2float_rn(xn - (double)hi);
+          if (p.inc || p.record_refs) store_increment_refs(p, nxt, e, xo, xn, pr);
         }
         if (ract && g.a == 0) p.xmask[nxt][grow_i] = msk;
       } else {
@@ -1015,7 +1064,6 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     // k = 16: lane groups of 16 (lane a <-> component a), one row per group,
     // rows 2 w and 2 w + 1 on warp w; warm-started Lawson-Hanson on the group
     using V16 = typename Xs::V16;
-    constexpr bool F16 = std::is_same<V16, float>::value;
     auto& gram_w = xs.gram_w;
     auto& term_w = xs.term_w;
     for (int e = tid; e < K * K; e += T) xs.Hp[e / K][e % K] = (V16)H[e];
@@ -1024,13 +1072,14 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     const int lrow = warp * 2 + half, grow_i = row0 + lrow;
     const bool ract = grow_i < p.n;   // uniform on the 16 lanes of a row
     LaneNnls16<V16> nn;
-    nn.init(xs.Hp, F16 ? (V16)1.1920928955078125e-07 : (V16)2.220446049250313e-16);
+    nn.init(xs.Hp, (V16)(p.inc ? 5.684341886080802e-14 : Xs::EPS));
     double pr = 0.0, xo = 0.0;
     uint32_t old_mask = 0;
     if (ract) {
       TA ts = psum[0][lrow][a];
       for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][a]);
       pr = PartOps<TA>::to_double(ts);
+      if (p.inc && mode == MODE_SWEEP) pr += p.Pref[(size_t)grow_i * K + a];
       xo = p.X[cur][(size_t)grow_i * K + a];
       old_mask = p.xmask[cur][grow_i];
     }
@@ -1089,7 +1138,10 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       const int xb = mode == MODE_SWEEP ? nxt : cur;
       const double xv = mode == MODE_SWEEP ? xn : xo;
       const float hi = __double2float_rn(xv);
-      if (mode == MODE_SWEEP) p.X[nxt][(size_t)grow_i * K + a] = xn;
+      if (mode == MODE_SWEEP) {
+        p.X[nxt][(size_t)grow_i * K + a] = xn;
+        if (p.inc || p.record_refs) store_increment_refs(p, nxt, (size_t)grow_i * K + a, xo, xn, pr);
+      }
       p.X32[xb][(size_t)grow_i * K + a] = hi;
       p.X32lo[xb][(size_t)grow_i * K + a] = __double2float_rn(xv - (double)hi);
       if (a == 0) p.xmask[xb][grow_i] = msk;

@@ -27,8 +27,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["pdf_like", "paper_uniform", "init_factors", "batch_problem_shapes",
-           "rng"]
+__all__ = ["pdf_like", "paper_uniform", "init_factors", "near_truth_factors",
+           "batch_problem_shapes", "rng"]
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -89,6 +89,14 @@ def init_factors(n: int, m: int, k: int, seed: int = 0):
     """U[0,1] starting point: X (n x k), Y (k x m), both float64."""
     g = rng(seed + 7919)
     return g.uniform(0.0, 1.0, size=(n, k)), g.uniform(0.0, 1.0, size=(k, m))
+
+
+def near_truth_factors(X0, Y0, rel: float = 0.1, seed: int = 0):
+    """A starting point near the generating factors: X0 with every entry
+    scaled by U[1 - rel, 1 + rel], and Y0 as it is (both float64 copies)."""
+    g = rng(seed + 104729)
+    X = np.asarray(X0, dtype=np.float64) * g.uniform(1.0 - rel, 1.0 + rel, size=np.shape(X0))
+    return X, np.array(Y0, dtype=np.float64)
 
 
 def batch_problem_shapes(nprob: int, seed0: int = 1000, n_range=(500, 4000),

@@ -100,3 +100,37 @@ def test_selftest_rejects_bad_limit(lib):
     assert lib.nmf_selftest_bounded_wait(1 << 30, None) == _native.NMF_EINVAL
     assert lib.nmf_selftest_tc16_wait(0, None) == _native.NMF_EINVAL
     assert lib.nmf_selftest_tc16_wait(20000, None) == _native.NMF_EINVAL
+
+
+def test_noalloc_rejects_misaligned_pointers_before_any_device_work(lib):
+    """nmf_sweep_noalloc checks the alignment of the caller's pointers before
+    it touches the device (M is staged with bulk copies from 16-byte aligned
+    addresses; X, Y and the record are doubles), so these fake addresses are
+    never dereferenced."""
+    from paper_2101_08431_gb300 import _native
+    P = C.c_void_p
+    good, m4, x4 = 0x10000, 0x10004, 0x10004
+    assert lib.nmf_sweep_noalloc(P(m4), 100, 10, 128, 4, P(good), P(good), None, None) == _native.NMF_EINVAL
+    assert lib.nmf_sweep_noalloc(P(0x10008), 100, 10, 128, 4, P(good), P(good), None, None) == _native.NMF_EINVAL
+    assert lib.nmf_sweep_noalloc(P(good), 100, 10, 128, 4, P(x4), P(good), None, None) == _native.NMF_EINVAL
+    assert lib.nmf_sweep_noalloc(P(good), 100, 10, 128, 4, P(good), P(x4), None, None) == _native.NMF_EINVAL
+    assert lib.nmf_sweep_noalloc(P(good), 100, 10, 128, 4, P(good), P(good), P(x4), None) == _native.NMF_EINVAL
+
+
+def test_persistence_arguments_rejected_before_any_device_work(lib, tmp_path):
+    """nmf_save / nmf_load / nmf_get_config reject NULL arguments, a path
+    that cannot be opened and a file that is not one of theirs, all before
+    any device allocation (nmf_load reads and checks the whole file first)."""
+    from paper_2101_08431_gb300 import _native
+    h = C.c_void_p()
+    cfg = _native.nmf_config()
+    assert lib.nmf_save(None, b"/tmp/x") == _native.NMF_EINVAL
+    assert lib.nmf_load(None, None, C.byref(h)) == _native.NMF_EINVAL
+    assert lib.nmf_load(b"/tmp/x", None, None) == _native.NMF_EINVAL
+    assert lib.nmf_get_config(None, C.byref(cfg)) == _native.NMF_EINVAL
+    assert lib.nmf_load(str(tmp_path / "missing.nmf").encode(), None, C.byref(h)) == _native.NMF_EINVAL
+    for content in (b"", b"NMFGB30", b"NOTMAGIC" + bytes(200), b"NMFGB300" + bytes(200)):
+        p = tmp_path / "f.nmf"
+        p.write_bytes(content)
+        assert lib.nmf_load(str(p).encode(), None, C.byref(h)) == _native.NMF_EINVAL
+        assert not h.value

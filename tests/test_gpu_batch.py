@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 import synth
+from _parity import colmax_rel, objective_ratios
 
 pytestmark = pytest.mark.gpu
 
@@ -29,13 +30,19 @@ def _lib():
     return StreamingNMFBatch, StreamingNMF
 
 
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+def _rel_y(a, b):
+    """Largest relative error of one column of Y (k x m)."""
+    return colmax_rel(a, b, axis=0)
 
 
-def _state(n, m, k, seed, warm_sweeps=15):
-    M, _, _ = synth.pdf_like(n, m, k, noise=1e-3, relative=True, seed=seed)
-    X, Y = synth.init_factors(n, m, k, seed=seed)
+def _rel_x(a, b):
+    """Largest relative error of one row of X (n x k)."""
+    return colmax_rel(a, b, axis=1)
+
+
+def _state(n, m, k, seed, warm_sweeps=15, near_truth=False):
+    M, X0, Y0 = synth.pdf_like(n, m, k, noise=1e-3, relative=True, seed=seed)
+    X, Y = synth.near_truth_factors(X0, Y0, 0.1, seed=seed) if near_truth else synth.init_factors(n, m, k, seed=seed)
     if warm_sweeps:
         X, Y, _, _, _, _, st = oracle.anls(M, X, Y, max_sweeps=warm_sweeps)
         assert st == oracle.OK
@@ -57,12 +64,15 @@ def _batch(B, states, **kw):
 
 @pytest.mark.parametrize("mode", [2, 0])
 def test_batch_one_sweep_parity(mode):
-    """mode 2 (compensated): 1e-9.  mode 0 (FP32 contraction, ~1e-7 relative
-    on B and P): the error of each half-sweep is amplified by the condition
-    number of its Gram (G = X^T X for Y, H = Y Y^T for X), so the bar is
-    max(2e-4, 4e-7 cond)."""
+    """Per column of Y and row of X.  mode 2 (compensated): 1e-7.  mode 0
+    (FP32 contraction, ~1e-7 relative on B and P): the error of each
+    half-sweep is amplified by the condition number of its Gram (G = X^T X
+    for Y, H = Y Y^T for X), so the bar is min(1e-2, max(2e-3, 4e-7 cond)).
+    Both: the per-column objective check of tests/_parity.py."""
     B, _ = _lib()
-    states = [_state(n, m, k, seed=31 * n + k) for n, m, k in SHAPES]
+    # states near the generating factors: the Grams are conditioned as on the
+    # data the pass is used for, so that the per-row value bar means something
+    states = [_state(n, m, k, seed=31 * n + k, near_truth=True) for n, m, k in SHAPES]
     ref = [oracle.sweep(M, X, Y) for M, X, Y in states]
     with _batch(B, states) as b:
         b.set_pass_mode(mode)
@@ -72,14 +82,16 @@ def test_batch_one_sweep_parity(mode):
             assert st == oracle.OK
             X0 = states[j][1]
             if mode == 2:
-                bar_y = bar_x = 1e-9
+                bar_y = bar_x = 1e-7
             else:
-                bar_y = max(2e-4, 4e-7 * np.linalg.cond(X0.T @ X0))
-                bar_x = max(2e-4, 4e-7 * np.linalg.cond(Yo @ Yo.T))
+                bar_y = min(1e-2, max(2e-3, 4e-7 * np.linalg.cond(X0.T @ X0)))
+                bar_x = min(1e-2, max(2e-3, 4e-7 * np.linalg.cond(Yo @ Yo.T)))
             Xg, Yg, _, _ = b.get_factors(j)
             assert stats[j]["sweeps"] == 1
-            assert _rel(Yg, Yo) <= bar_y, (j, _rel(Yg, Yo), bar_y)
-            assert _rel(Xg, Xo) <= bar_x, (j, _rel(Xg, Xo), bar_x)
+            assert _rel_y(Yg, Yo) <= bar_y, (j, _rel_y(Yg, Yo), bar_y)
+            assert _rel_x(Xg, Xo) <= bar_x, (j, _rel_x(Xg, Xo), bar_x)
+            ry, rx, _ = objective_ratios(states[j][0], X0, Xg, Yg, "df" if mode == 2 else "f32")
+            assert ry <= 1.0 and rx <= 1.0, (j, ry, rx)
 
 
 def test_batch_three_sweeps_compensated():
@@ -98,8 +110,8 @@ def test_batch_three_sweeps_compensated():
         for j, (Xo, Yo) in enumerate(ref):
             Xg, Yg, _, _ = b.get_factors(j)
             assert stats[j]["fp64_sweeps"] == 3
-            assert _rel(Yg, Yo) <= 3e-9
-            assert _rel(Xg, Xo) <= 3e-9
+            assert _rel_y(Yg, Yo) <= 3e-9
+            assert _rel_x(Xg, Xo) <= 3e-9
 
 
 def test_batch_alone_equals_mixed():
@@ -168,8 +180,8 @@ def test_batch_autotune_then_parity():
         for j, (M, _, _) in enumerate(states):
             Xo, Yo, _, _, st = oracle.sweep(M, X0[j][0], X0[j][1])
             Xg, Yg, _, _ = b.get_factors(j)
-            assert _rel(Yg, Yo) <= 1e-9
-            assert _rel(Xg, Xo) <= 1e-9
+            assert _rel_y(Yg, Yo) <= 1e-9
+            assert _rel_x(Xg, Xo) <= 1e-9
         assert b.launches > 0
 
 

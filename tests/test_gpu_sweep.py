@@ -1,14 +1,20 @@
 """GPU parity of the ANLS sweep against the CPU oracle, through the C ABI.
 
-Bars (the rounding of each pass's contraction, ~1e-16 FP64, ~1e-13
-double-float, ~1e-7 FP32 relative, amplified by the condition number of the
-half-sweep's Gram, with margin):
+Every comparison is per column of Y and per row of X (the largest relative
+error of one column / row, columns below 1e-3 of the largest measured
+against 1e-3 of it), so a few wrong small columns cannot hide in a norm of
+the whole factor.  Bars (the rounding of each pass's contraction, ~1e-16
+FP64, ~1e-13 double-float, ~1e-7 FP32 relative, amplified by the condition
+number of the half-sweep's Gram and, per column, by the cancellation in its
+right-hand side, with margin):
 * FP64 form and FP64-accumulated passes: one sweep from the same state
-  agrees with the oracle to relative 1e-10 (Frobenius) on X and Y, and the
-  passive sets agree except on degenerate entries;
-* compensated FP32 (double-float) refinement passes of the mixed form: 1e-9;
-* FP32 passes: relative 2e-4 on Y and X after one sweep (FP32 contraction,
-  cond(G) amplification), passive sets agree except near-degenerate entries;
+  agrees with the oracle to 1e-9 per column and row, and the passive sets
+  agree except on degenerate entries;
+* compensated FP32 (double-float) refinement passes of the mixed form: 1e-7;
+* FP32 passes: 2e-3 after one sweep;
+* per column and row, the subproblem's objective (eq. "qp") of the GPU's
+  solution is within the first-order bound of its pass's rounding of the
+  optimum the oracle finds for the same subproblem (tests/_parity.py);
 * statistics of the iterate (f, KKT) agree with the oracle's direct
   computation from the residual.
 Each case starts from a state reached by oracle sweeps, so that the
@@ -20,6 +26,7 @@ import pytest
 
 import oracle
 import synth
+from _parity import colmax_rel, objective_ratios
 
 pytestmark = pytest.mark.gpu
 
@@ -35,13 +42,26 @@ def _lib():
     return StreamingNMF
 
 
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+def _rel_y(a, b):
+    """Largest relative error of one column of Y (k x m)."""
+    return colmax_rel(a, b, axis=0)
 
 
-def _state(n, m, k, seed, warm_sweeps=15, noise=1e-3):
-    M, _, _ = synth.pdf_like(n, m, k, noise=noise, relative=True, seed=seed)
-    X, Y = synth.init_factors(n, m, k, seed=seed)
+def _rel_x(a, b):
+    """Largest relative error of one row of X (n x k)."""
+    return colmax_rel(a, b, axis=1)
+
+
+def _objective(M, X, Xg, Yg, kind):
+    """Per column and row: the subproblem objective within its first-order
+    bound of the pass's rounding (both halves)."""
+    ry, rx, _ = objective_ratios(M, X, Xg, Yg, kind)
+    assert ry <= 1.0 and rx <= 1.0, (kind, ry, rx)
+
+
+def _state(n, m, k, seed, warm_sweeps=15, noise=1e-3, near_truth=False):
+    M, X0, Y0 = synth.pdf_like(n, m, k, noise=noise, relative=True, seed=seed)
+    X, Y = synth.near_truth_factors(X0, Y0, 0.1, seed=seed) if near_truth else synth.init_factors(n, m, k, seed=seed)
     if warm_sweeps:
         X, Y, _, _, _, _, st = oracle.anls(M, X, Y, max_sweeps=warm_sweeps)
         assert st == oracle.OK
@@ -84,8 +104,9 @@ def test_fp64_one_sweep_parity(n, m, k):
     with _handle(S, M, X, Y, PREC_FP64) as h:
         h.sweep(1)
         Xg, Yg, xmg, ymg = h.get_factors()
-    assert _rel(Yg, Yo) <= 1e-10
-    assert _rel(Xg, Xo) <= 1e-10
+    assert _rel_y(Yg, Yo) <= 1e-9
+    assert _rel_x(Xg, Xo) <= 1e-9
+    _objective(M, X, Xg, Yg, "fp64")
     assert _masks_agree(Yg, ymg, Yo, 1e-9)
     assert _masks_agree(Xg.T, xmg, Xo.T, 1e-9)
 
@@ -100,24 +121,27 @@ def test_refinement_pass_one_sweep_parity(n, m, k):
     with _handle(S, M, X, Y, PREC_MIXED, mode=1) as h:
         h.sweep(1)
         Xg, Yg, xmg, ymg = h.get_factors()
-    assert _rel(Yg, Yo) <= 1e-10
-    assert _rel(Xg, Xo) <= 1e-10
+    assert _rel_y(Yg, Yo) <= 1e-9
+    assert _rel_x(Xg, Xo) <= 1e-9
+    _objective(M, X, Xg, Yg, "fp64")
 
 
 @pytest.mark.parametrize("n,m,k", CASES)
 def test_compensated_pass_one_sweep_parity(n, m, k):
     """The compensated FP32 (double-float) contraction of the mixed form's
     refinement sweeps carries ~44-46 significant bits (B and P to ~1e-13
-    relative); one sweep agrees with the FP64 oracle to 1e-9, the mixed
-    form's stated bar for it (1e-13 amplified by cond(H) <= ~1e4 at k = 8)."""
+    relative); one sweep agrees with the FP64 oracle to 1e-7 per column and
+    row (1e-13 amplified by cond(H) <= ~1e4 at k = 8 and by the cancellation
+    in a small column's right-hand side)."""
     S = _lib()
     M, X, Y = _state(n, m, k, seed=5 * n + k)
     Xo, Yo, _, _, _ = oracle.sweep(M, X, Y)
     with _handle(S, M, X, Y, PREC_MIXED, mode=2) as h:
         h.sweep(1)
         Xg, Yg, xmg, ymg = h.get_factors()
-    assert _rel(Yg, Yo) <= 1e-9
-    assert _rel(Xg, Xo) <= 1e-9
+    assert _rel_y(Yg, Yo) <= 1e-7
+    assert _rel_x(Xg, Xo) <= 1e-7
+    _objective(M, X, Xg, Yg, "df")
     assert _masks_agree(Yg, ymg, Yo, 1e-9)
 
 
@@ -129,9 +153,35 @@ def test_fp32_pass_one_sweep(n, m, k):
     with _handle(S, M, X, Y, PREC_MIXED, mode=0) as h:
         h.sweep(1)
         Xg, Yg, xmg, ymg = h.get_factors()
-    assert _rel(Yg, Yo) <= 2e-4
-    assert _rel(Xg, Xo) <= 2e-4
+    assert _rel_y(Yg, Yo) <= 2e-3
+    assert _rel_x(Xg, Xo) <= 2e-3
+    _objective(M, X, Xg, Yg, "f32")
     assert _masks_agree(Yg, ymg, Yo, 1e-3)
+
+
+@pytest.mark.parametrize("n,m,k", CASES[:4] + [(800, 100, 16)])
+def test_incremental_chunk_tracks_the_oracle(n, m, k):
+    """Pass mode 3: one chunk of 32 sweeps, a compensated sweep that records
+    the reference contractions and 31 incremental sweeps (FP32 contraction
+    of the change of X and Y since the references).  It tracks 32 oracle
+    sweeps, and 32 compensated sweeps, to 1e-7 per column and row, from a
+    state of the refinement phase (near the generating factors, after oracle
+    sweeps): there the change of X and Y over a chunk is small, so the FP32
+    contraction of the change is FP64-accurate."""
+    S = _lib()
+    M, X, Y = _state(n, m, k, seed=11 * n + k, warm_sweeps=100, near_truth=True)
+    Xo, Yo, _, _, _, _, st = oracle.anls(M, X, Y, max_sweeps=32)
+    assert st == oracle.OK
+    out = {}
+    for mode in (3, 2):
+        with _handle(S, M, X, Y, PREC_MIXED, mode=mode) as h:
+            stt = h.sweep(32)
+            assert stt["sweeps"] == 32 and stt["fp64_sweeps"] == 32
+            out[mode] = h.get_factors()
+    (Xi, Yi, _, ymi), (Xd, Yd, _, _) = out[3], out[2]
+    assert _rel_y(Yi, Yo) <= 1e-7 and _rel_x(Xi, Xo) <= 1e-7, (_rel_y(Yi, Yo), _rel_x(Xi, Xo))
+    assert _rel_y(Yi, Yd) <= 1e-7 and _rel_x(Xi, Xd) <= 1e-7
+    assert _masks_agree(Yi, ymi, Yo, 1e-9)
 
 
 def test_ten_fp64_sweeps_track_the_oracle():
@@ -141,7 +191,7 @@ def test_ten_fp64_sweeps_track_the_oracle():
     with _handle(S, M, X, Y, PREC_FP64) as h:
         h.sweep(10)
         Xg, Yg, _, _ = h.get_factors()
-    assert _rel(Yg, Yo) <= 1e-9 and _rel(Xg, Xo) <= 1e-9
+    assert _rel_y(Yg, Yo) <= 1e-9 and _rel_x(Xg, Xo) <= 1e-9
 
 
 @pytest.mark.parametrize("prec,mode", [(PREC_FP64, None), (PREC_MIXED, 1)])
@@ -212,6 +262,32 @@ def test_mixed_run_to_target_beats_fp32_floor():
     assert oracle.kkt(M, Xg, Yg)["rel"] <= 1.05e-8
 
 
+def test_incremental_run_to_target_matches_compensated_run():
+    """From the same start, the automatic schedule (FP32 sweeps, then chunks of
+    a reference-recording compensated sweep and incremental sweeps) and the
+    compensated pass alone reach relative KKT 1e-8 at iterates the oracle
+    certifies.  (Their objectives agree to 1e-6: two points of the same
+    valley that both meet the KKT target, on different trajectories.)"""
+    S = _lib()
+    n, m, k = 700, 260, 4
+    M, _, _ = synth.pdf_like(n, m, k, noise=1e-3, relative=True, seed=6)
+    X, Y = synth.init_factors(n, m, k, seed=6)
+    res = {}
+    for mode in (-1, 2):
+        h = S(n, k, m, prec=PREC_MIXED, kkt_target=1e-8, max_sweeps=40000)
+        h.append_columns(np.asfortranarray(M.astype(np.float32)))
+        h.set_factors(X, Y)
+        h.set_pass_mode(mode)
+        stt = h.sweep(0)
+        Xg, Yg, _, _ = h.get_factors()
+        h.close()
+        assert stt["converged"] == 1
+        assert oracle.kkt(M, Xg, Yg)["rel"] <= 1.05e-8
+        res[mode] = oracle.objective(M, Xg, Yg)
+    print("objectives: automatic %.12e, compensated %.12e" % (res[-1], res[2]))
+    assert res[-1] == pytest.approx(res[2], rel=1e-6)
+
+
 def test_edge_cases():
     S = _lib()
     rs = np.random.default_rng(0)
@@ -224,7 +300,7 @@ def test_edge_cases():
         with _handle(S, M, X, Y, PREC_FP64) as h:
             h.sweep(1)
             Xg, Yg, _, _ = h.get_factors()
-        assert _rel(Yg, Yo) <= 1e-10 and _rel(Xg, Xo) <= 1e-10
+        assert _rel_y(Yg, Yo) <= 1e-10 and _rel_x(Xg, Xo) <= 1e-10
     # an all-zero column of M gives y = 0
     M, X, Y = _state(300, 40, 3, seed=5)
     M[:, 7] = 0.0
@@ -233,7 +309,7 @@ def test_edge_cases():
         h.sweep(1)
         Xg, Yg, _, ymg = h.get_factors()
     assert np.all(Yg[:, 7] == 0) and ymg[7] == 0
-    assert _rel(Yg, Yo) <= 1e-10
+    assert _rel_y(Yg, Yo) <= 1e-10
 
 
 def test_ring_buffer_append_and_evict():
@@ -255,7 +331,7 @@ def test_ring_buffer_append_and_evict():
     h.sweep(1)
     Xg2, Yg2, _, _ = h.get_factors()
     h.close()
-    assert _rel(Yg2, Yo) <= 1e-10 and _rel(Xg2, Xo) <= 1e-10
+    assert _rel_y(Yg2, Yo) <= 1e-10 and _rel_x(Xg2, Xo) <= 1e-10
 
 
 def test_nonfinite_input_is_reported():
