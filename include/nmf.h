@@ -229,6 +229,45 @@ nmf_status nmf_get_timing(nmf_handle *h, double *ypass_ms, int64_t *ypass_launch
 nmf_status nmf_save(nmf_handle *h, const char *path);
 nmf_status nmf_load(const char *path, void *cuda_stream, nmf_handle **out);
 
+/* Multi-GPU: the time columns sharded across ranks (one process, GPU and
+ * handle per rank; each handle holds its own columns, appended as usual, and
+ * the same X).  In Alg. "anls" (Sec. 2) the Y half solves every column on its
+ * own, and the X half needs only P = M Y^T and H = Y Y^T summed over all
+ * columns, so a sweep is:
+ *   1. nmf_shard_y_half on every rank: the M pass over the rank's columns
+ *      (new Y, passive sets) and the rank's P (n x k, row-major), H (k x k),
+ *      Y-half KKT terms and ||M||^2, written to sum_buf
+ *      (nmf_shard_buffer_len(n, k) doubles) and the largest y to max_buf
+ *      (1 double);
+ *   2. the caller's collective: sum_buf summed over the ranks, max_buf its
+ *      maximum (e.g. two NCCL or gloo all-reduces) -- the one exchange of the
+ *      sweep, n k + k^2 + 11 doubles;
+ *   3. nmf_shard_x_half on every rank with the reduced buffers: the row pass
+ *      (the same X on every rank, as all-reduce results are the same on every
+ *      rank), G = X^T X, and the statistics of the incoming iterate over the
+ *      whole problem (stats may be NULL; filling it synchronises; the first
+ *      sweep after nmf_set_factors reports its incoming iterate unmeasured,
+ *      kkt_rel = -1, as the priming pass saw only the rank's columns).
+ * Pass: the FP64 form's pass; for NMF_PREC_MIXED handles pass mode 0 (FP32),
+ * 1 (FP64-accumulated), else the compensated pass.  Buffers are host memory
+ * (on_device 0; the calls then synchronise the stream) or device memory
+ * (on_device 1).  The stopping tests apply to the whole problem
+ * (stats.converged).  Errors: NMF_EINVAL for NULL pointers, NMF_ESTATE for a
+ * Y half before factors are set, two Y halves in a row or an X half without
+ * one. */
+int64_t nmf_shard_buffer_len(int64_t n, int32_t k);
+nmf_status nmf_shard_y_half(nmf_handle *h, double *sum_buf, double *max_buf, int32_t on_device);
+nmf_status nmf_shard_x_half(nmf_handle *h, const double *sum_buf, const double *max_buf, int32_t on_device,
+                            nmf_stats *stats);
+
+/* The accumulated device time (ms) of the M passes and of the row passes
+ * of one pass variant since nmf_set_timing(h, 1), and how many sweeps ran
+ * it: pass 0 FP32, 1 FP64-accumulated, 2 compensated, 3 incremental (pass
+ * modes 0..3 of the mixed form), 4 the FP64 form's pass.  Synchronises the
+ * stream.  Any output pointer may be NULL; NMF_EINVAL for another pass. */
+nmf_status nmf_get_pass_timing(nmf_handle *h, int32_t pass, double *ypass_ms, double *xpass_ms,
+                               int64_t *sweeps);
+
 /* One ANLS sweep that allocates no memory at all.
  *
  * The paper has no counterpart: this is a deployment variant of nmf_sweep for

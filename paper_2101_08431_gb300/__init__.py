@@ -127,9 +127,38 @@ class StreamingNMF:
         return {"ypass_ms": ym.value, "ypass_launches": yl.value, "xpass_ms": xm.value,
                 "xpass_launches": xl.value}
 
+    PASSES = {"f32": 0, "ref": 1, "df": 2, "inc": 3, "f64": 4}
+
+    def get_pass_timing(self, name):
+        """Device time of one pass variant's M and row passes since
+        set_timing(True): {"ypass_ms", "xpass_ms", "sweeps"}."""
+        ym, xm, n = C.c_double(), C.c_double(), C.c_int64()
+        check(self.lib.nmf_get_pass_timing(self.h, self.PASSES[name], C.byref(ym), C.byref(xm), C.byref(n)),
+              self.h)
+        return {"ypass_ms": ym.value, "xpass_ms": xm.value, "sweeps": n.value}
+
     @property
     def launches(self):
         return int(self.lib.nmf_launch_count(self.h))
+
+    # -- column sharding (one rank's share of a multi-GPU sweep) ----------------
+    def shard_y_half(self):
+        """The Y half on this handle's columns; returns (sum_buf, max_buf),
+        host arrays to be all-reduced (sum, max) across the ranks."""
+        n = int(self.lib.nmf_shard_buffer_len(self.n, self.k))
+        sb, mb = np.zeros(n), np.zeros(1)
+        check(self.lib.nmf_shard_y_half(self.h, C.c_void_p(sb.ctypes.data), C.c_void_p(mb.ctypes.data), 0), self.h)
+        return sb, mb
+
+    def shard_x_half(self, sum_buf, max_buf):
+        """The X half from the all-reduced buffers; returns the statistics of
+        the incoming iterate over the whole problem."""
+        sb = np.ascontiguousarray(sum_buf, dtype=np.float64)
+        mb = np.ascontiguousarray(max_buf, dtype=np.float64)
+        st = nmf_stats()
+        check(self.lib.nmf_shard_x_half(self.h, C.c_void_p(sb.ctypes.data), C.c_void_p(mb.ctypes.data), 0,
+                                        C.byref(st)), self.h)
+        return st.as_dict()
 
     # -- persistence ------------------------------------------------------------
     def save(self, path):

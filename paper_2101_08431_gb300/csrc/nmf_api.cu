@@ -79,9 +79,9 @@ __global__ void seed_kernel(DevState* st, const double* Y0, const double* Y1, co
   if (threadIdx.x == 0) *seed_mask = ym[phys];
 }
 
-// ||M||^2 of the resident window (fixed order) and invalidation of the X-half
-// terms of the current iterate (P = M Y^T changed).
-__global__ void msq_kernel(DevState* st, const double* colsq, int head, int m, int mcap) {
+// ||M||^2 of the resident window (fixed order) and, with invalidate, of the
+// X-half terms of the current iterate (P = M Y^T changed).
+__global__ void msq_kernel(DevState* st, const double* colsq, int head, int m, int mcap, int invalidate = 1) {
   __shared__ double red[256];
   double t = 0.0;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -97,8 +97,10 @@ __global__ void msq_kernel(DevState* st, const double* colsq, int head, int m, i
   }
   if (threadIdx.x == 0) {
     st->msq = red[0];
-    st->xiter[0][XT_VALID] = 0.0;
-    st->xiter[1][XT_VALID] = 0.0;
+    if (invalidate) {
+      st->xiter[0][XT_VALID] = 0.0;
+      st->xiter[1][XT_VALID] = 0.0;
+    }
   }
 }
 
@@ -119,6 +121,65 @@ __global__ void kkt_stats_kernel(Problem p, int Q, double* out) {
   if (tid < 32) {
     const int iter = st->iter;
     combine_stats_warp(yfin, st->xiter[iter & 1], st->msq, -1.0, iter, p.fp64_pass, out);
+  }
+}
+
+// Column sharding: this rank's contribution to the X half of a sweep, in
+// fixed order -- P = sum over the Q column groups of the partials of
+// M_shard Y_shard^T (n x k), H = Y_shard Y_shard^T, the Y-half terms, and the
+// shard's ||M||^2 -- into out[]; the largest y into outmax[0].
+template <typename TA>
+__global__ void shard_export_kernel(Problem p, int Q, double* out, double* outmax) {
+  using PO = PartOps<TA>;
+  const TA* Pp = static_cast<const TA*>(p.Ppart);
+  const int k = p.k;
+  const long long nk = (long long)p.n * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / k, a = e % k;
+    TA acc = PO::zero();
+    for (int q = 0; q < Q; ++q) acc = PO::add(acc, Pp[((size_t)q * p.ld + row) * k + a]);
+    out[e] = PO::to_double(acc);
+  }
+  if (blockIdx.x != 0) return;
+  for (int e = threadIdx.x; e < k * k + NYT + 1; e += blockDim.x) {
+    double r = 0.0;
+    if (e < k * k) {
+      for (int q = 0; q < Q; ++q) r += p.Hpart[(size_t)q * k * k + e];
+    } else if (e < k * k + NYT) {
+      const int t = e - k * k;
+      for (int q = 0; q < Q; ++q) {
+        const double w = p.Yterms[(size_t)q * NYT + t];
+        r = (t == YT_YMAX) ? fmax(r, w) : r + w;
+      }
+      if (t == YT_YMAX) {
+        outmax[0] = r;
+        r = 0.0;
+      }
+    } else {
+      for (int j = 0; j < p.m; ++j) r += p.colsq[wrap_col(p.head, j, p.mcap)];
+    }
+    out[nk + e] = r;
+  }
+}
+
+// The all-reduced buffers into the row pass's inputs (one partial, FP64):
+// P rows, H, the Y-half terms (the largest y from inmax), and the global
+// ||M||^2 into the control block for the objective of this sweep's record.
+__global__ void shard_import_kernel(const double* in, const double* inmax, int n, int k, double* P, double* H,
+                                    double* Yterms, DevState* st) {
+  const long long nk = (long long)n * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk;
+       e += (long long)gridDim.x * blockDim.x)
+    P[e] = in[e];
+  if (blockIdx.x != 0) return;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) H[e] = in[nk + e];
+  for (int t = threadIdx.x; t < NYT; t += blockDim.x) Yterms[t] = (t == YT_YMAX) ? inmax[0] : in[nk + k * k + t];
+  if (threadIdx.x == 0) {
+    st->msq = in[nk + k * k + NYT];
+    // the X-half terms of iterate 0 came from the priming pass over this
+    // rank's columns alone: its record is marked unmeasured
+    if (st->iter == 0) st->xiter[0][XT_VALID] = 0.0;
   }
 }
 
@@ -172,6 +233,11 @@ struct nmf_handle {
   double* dXref = nullptr;
   float* dXd32[2] = {nullptr, nullptr};
   bool inc_ok = false;            // the incremental pass has a plan for this shape
+  // column sharding: exchange staging (out: sum part, max part) and the
+  // imported row-pass inputs
+  double* dShard = nullptr;
+  double* dShardP = nullptr;
+  int shard_var = -1;             // pass variant of the pending Y half (-1: none)
   DevState* hSt = nullptr;      // pinned mirror
   double* hKkt = nullptr;
   unsigned* hNonfinite = nullptr;
@@ -205,9 +271,12 @@ struct nmf_handle {
   bool timing = false;
   static constexpr int NEV = 512;
   cudaEvent_t ev[NEV][3] = {};
+  int ev_var[NEV] = {};
   int nev = 0;
   double y_ms = 0.0, x_ms = 0.0;
   int64_t y_launches = 0, x_launches = 0;
+  double yv_ms[NVAR] = {}, xv_ms[NVAR] = {};   // the same, per pass variant
+  int64_t v_launches[NVAR] = {};
 };
 
 namespace {
@@ -318,6 +387,9 @@ nmf_status drain_timing(nmf_handle* h) {
     CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[i][1], h->ev[i][2]));
     h->y_ms += a;
     h->x_ms += b;
+    h->yv_ms[h->ev_var[i]] += a;
+    h->xv_ms[h->ev_var[i]] += b;
+    h->v_launches[h->ev_var[i]]++;
   }
   h->y_launches += h->nev;
   h->x_launches += h->nev;
@@ -352,6 +424,7 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
   if (timed) {
     if (!h->ev[h->nev][0])
       for (int j = 0; j < 3; ++j) CUDA_TRY(h, cudaEventCreate(&h->ev[h->nev][j]));
+    h->ev_var[h->nev] = var;
     CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][0], h->stream));
   }
   if (use_tc) CUDA_TRY(h, tc16_launch(p, mode, T, h->stream));
@@ -530,7 +603,8 @@ nmf_status nmf_destroy(nmf_handle* h) {
   void* dptrs[] = {h->dM, h->dX[0], h->dX[1], h->dX32[0], h->dX32[1], h->dX32lo[0], h->dX32lo[1], h->dY[0], h->dY[1],
                    h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dHg, h->dHtab, h->dHok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
-                   h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1]};
+                   h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1],
+                   h->dShard, h->dShardP};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->hSt) cudaFreeHost(h->hSt);
@@ -817,6 +891,10 @@ nmf_status nmf_set_timing(nmf_handle* h, int32_t on) {
   h->timing = on != 0;
   h->y_ms = h->x_ms = 0.0;
   h->y_launches = h->x_launches = 0;
+  for (int v = 0; v < NVAR; ++v) {
+    h->yv_ms[v] = h->xv_ms[v] = 0.0;
+    h->v_launches[v] = 0;
+  }
   return NMF_OK;
 }
 
@@ -830,6 +908,111 @@ nmf_status nmf_get_timing(nmf_handle* h, double* ypass_ms, int64_t* ypass_launch
   if (ypass_launches) *ypass_launches = h->y_launches;
   if (xpass_ms) *xpass_ms = h->x_ms;
   if (xpass_launches) *xpass_launches = h->x_launches;
+  return NMF_OK;
+}
+
+int64_t nmf_shard_buffer_len(int64_t n, int32_t k) {
+  if (n < 1 || k < 1) return 0;
+  return n * k + (int64_t)k * k + NYT + 1;
+}
+
+nmf_status nmf_shard_y_half(nmf_handle* h, double* sum_buf, double* max_buf, int32_t on_device) {
+  if (!h || !sum_buf || !max_buf) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (!h->factors_set) return fail(h, NMF_ESTATE, "factors not set");
+  if (h->shard_var >= 0) return fail(h, NMF_ESTATE, "the previous Y half has not been completed");
+  // FP64 form: the FP64 pass; mixed: the pass mode's contraction (automatic
+  // and incremental modes use the compensated one)
+  int var = VAR_F64;
+  if (h->store_f32) var = h->forced_mode == 0 ? VAR_F32 : (h->forced_mode == 1 ? VAR_REF : VAR_DF);
+  if (!h->refine_ok && var != VAR_F32) var = VAR_F32;
+  const size_t len = (size_t)nmf_shard_buffer_len(h->n, h->k);
+  if (!h->dShard) {
+    CUDA_TRY(h, cudaMalloc(&h->dShard, sizeof(double) * (len + 1)));
+    CUDA_TRY(h, cudaMalloc(&h->dShardP, sizeof(double) * ((size_t)h->ld * h->k + h->k * h->k + NYT)));
+  }
+  YPlan L{};
+  Tc16Plan T{};
+  const bool use_tc = h->tc16 && var == VAR_F32;
+  if (use_tc) {
+    if (h->tc16_m != h->m) {
+      if (!tc16_plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
+        return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
+      h->tc16_m = h->m;
+    }
+    T = h->tc16_L;
+    L.Q = T.Q;
+  } else if (!make_plan(h, var, &L)) {
+    return fail(h, NMF_EINVAL, "no launch plan for this shape");
+  }
+  Problem p = make_problem(h, var);
+  CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
+  if (use_tc) CUDA_TRY(h, tc16_launch(p, MODE_SWEEP, T, h->stream));
+  else CUDA_TRY(h, h->ks[var].ypass(p, MODE_SWEEP, L, h->stream));
+  double* out = h->dShard;
+  double* outmax = h->dShard + len;
+  const int nb = std::max(1, std::min(h->nsm, (int)(((size_t)h->n * h->k + 255) / 256)));
+  if (var == VAR_F32) shard_export_kernel<float><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
+  else if (var == VAR_DF) shard_export_kernel<DF><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
+  else shard_export_kernel<double><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
+  h->launches += 2;
+  CUDA_TRY(h, cudaGetLastError());
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(h, cudaMemcpyAsync(sum_buf, out, sizeof(double) * len, kind, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(max_buf, outmax, sizeof(double), kind, h->stream));
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->shard_var = var;
+  h->snap_valid = false;
+  return NMF_OK;
+}
+
+nmf_status nmf_shard_x_half(nmf_handle* h, const double* sum_buf, const double* max_buf, int32_t on_device,
+                            nmf_stats* stats) {
+  if (!h || !sum_buf || !max_buf) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (h->shard_var < 0) return fail(h, NMF_ESTATE, "no Y half is pending");
+  const size_t len = (size_t)nmf_shard_buffer_len(h->n, h->k);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(h, cudaMemcpyAsync(h->dShard, sum_buf, sizeof(double) * len, kind, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->dShard + len, max_buf, sizeof(double), kind, h->stream));
+  double* P = h->dShardP;
+  double* H = P + (size_t)h->ld * h->k;
+  double* Yt = H + h->k * h->k;
+  const int nb = std::max(1, std::min(h->nsm, (int)(((size_t)h->n * h->k + 255) / 256)));
+  shard_import_kernel<<<nb, 256, 0, h->stream>>>(h->dShard, h->dShard + len, h->n, h->k, P, H, Yt, h->dSt);
+  // the FP64-class row pass on the global P and H (one partial)
+  const int var_x = h->store_f32 ? VAR_REF : VAR_F64;
+  Problem p = make_problem(h, h->shard_var);
+  p.Ppart = P;
+  p.Hpart = H;
+  p.Yterms = Yt;
+  p.fp64_pass = h->shard_var != VAR_F32;
+  CUDA_TRY(h, h->ks[var_x].xpass(p, MODE_SWEEP, 1, h->nxblk, h->stream));
+  h->launches += 2;
+  CUDA_TRY(h, cudaGetLastError());
+  h->shard_var = -1;
+  // the control block holds this rank's own ||M||^2 again (nmf_objective_kkt
+  // measures the rank's own columns)
+  msq_kernel<<<1, 256, 0, h->stream>>>(h->dSt, h->dColsq, h->head, h->m, h->mcap, 0);
+  h->launches++;
+  nmf_status s = read_state(h);
+  if (s != NMF_OK) return s;
+  if (stats) fill_stats(h, h->hSt->done && h->hSt->stop_reason == 1 ? h->hSt->iter : h->hSt->iter - 1, 1,
+                        p.fp64_pass, stats);
+  return NMF_OK;
+}
+
+nmf_status nmf_get_pass_timing(nmf_handle* h, int32_t pass, double* ypass_ms, double* xpass_ms,
+                               int64_t* sweeps) {
+  static const int var_of[5] = {VAR_F32, VAR_REF, VAR_DF, VAR_INC, VAR_F64};
+  if (!h || pass < 0 || pass > 4) return NMF_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  nmf_status s = drain_timing(h);
+  if (s != NMF_OK) return s;
+  const int v = var_of[pass];
+  if (ypass_ms) *ypass_ms = h->yv_ms[v];
+  if (xpass_ms) *xpass_ms = h->xv_ms[v];
+  if (sweeps) *sweeps = h->v_launches[v];
   return NMF_OK;
 }
 
