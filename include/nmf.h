@@ -65,7 +65,12 @@ typedef enum {
 } nmf_precision;
 
 enum { NMF_DTYPE_F64 = 0, NMF_DTYPE_F32 = 1 };
-enum { NMF_WARM_COLD = 0, NMF_WARM_PREV = 1 };
+/* Warm start of the column solves (Sec. 2): cold; from the column's own
+ * previous-sweep solution (all columns in parallel); or the paper's chain,
+ * column j from column j - 1's new solution, one column after another over
+ * the whole window (one CTA; k <= 8 -- rank 16 solves from the previous
+ * sweep) -- the sequential form whose active-set savings Sec. 2 argues for. */
+enum { NMF_WARM_COLD = 0, NMF_WARM_PREV = 1, NMF_WARM_CHAIN = 2 };
 
 typedef struct {
     int64_t n;               /* rows of M (distance grid)                     */
@@ -79,8 +84,11 @@ typedef struct {
     double mixed_switch;     /* MIXED: move to the refinement passes once the
                                 relative KKT error <= this (or stalls)       */
     int32_t max_sweeps;      /* cap for nmf_sweep(h, 0, ...)                  */
-    int32_t warm_start;      /* NMF_WARM_COLD or NMF_WARM_PREV                */
+    int32_t warm_start;      /* NMF_WARM_COLD, NMF_WARM_PREV or NMF_WARM_CHAIN */
     void *cuda_stream;       /* cudaStream_t, or NULL                         */
+    double kkt_abs_target;   /* also stop when the absolute KKT error E (Sec.
+                                5.1's stopping rule, eps_TOL) <= this; <= 0
+                                disables                                      */
 } nmf_config;
 
 typedef struct {
@@ -99,11 +107,12 @@ typedef struct {
     int64_t changed_rows;    /* rows whose passive set changed (last sweep)    */
     int64_t nnls_notconv;    /* NNLS solves that hit their iteration cap       */
     int32_t measured_iter;   /* iterate the f / KKT figures belong to          */
-    int32_t pad;
+    int32_t entering_steps;  /* Lawson-Hanson entering steps of the column
+                                solves of the sweep that measured the record  */
 } nmf_stats;
 
-/* Defaults: stol 0, kkt_target 1e-8, mixed_switch 1e-6, max_sweeps 100000,
- * warm_start NMF_WARM_PREV, prec NMF_PREC_MIXED. */
+/* Defaults: stol 0, kkt_target 1e-8, kkt_abs_target 0, mixed_switch 1e-6,
+ * max_sweeps 100000, warm_start NMF_WARM_PREV, prec NMF_PREC_MIXED. */
 void nmf_config_init(nmf_config *cfg);
 
 /* Create a handle for one problem of n rows, rank k and up to m_capacity

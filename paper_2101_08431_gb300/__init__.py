@@ -14,10 +14,10 @@ import numpy as np
 
 from . import _native
 from ._native import (NMF_DTYPE_F32, NMF_DTYPE_F64, NMF_PREC_FP64, NMF_PREC_MIXED, NMF_WARM_COLD,
-                      NMF_WARM_PREV, NMFError, check, load, nmf_config, nmf_stats)
+                      NMF_WARM_CHAIN, NMF_WARM_PREV, NMFError, check, load, nmf_config, nmf_stats)
 
 __all__ = ["StreamingNMF", "StreamingNMFBatch", "StreamingServer", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
-           "NMF_PREC_MIXED", "NMF_DTYPE_F32", "NMF_DTYPE_F64", "NMF_WARM_COLD", "NMF_WARM_PREV"]
+           "NMF_PREC_MIXED", "NMF_DTYPE_F32", "NMF_DTYPE_F64", "NMF_WARM_COLD", "NMF_WARM_PREV", "NMF_WARM_CHAIN"]
 
 
 def _ptr(a):
@@ -59,7 +59,7 @@ class StreamingNMF:
     """One problem: min 1/2||XY - M||^2, X, Y >= 0, columns of M appended over time."""
 
     def __init__(self, n, k, m_capacity, prec=NMF_PREC_MIXED, kkt_target=1e-8, stol=0.0,
-                 mixed_switch=1e-6, max_sweeps=100000, warm_start=NMF_WARM_PREV, stream=None):
+                 mixed_switch=1e-6, max_sweeps=100000, warm_start=NMF_WARM_PREV, stream=None, kkt_abs_target=0.0):
         self.lib = load()
         cfg = nmf_config()
         self.lib.nmf_config_init(C.byref(cfg))
@@ -67,6 +67,7 @@ class StreamingNMF:
         cfg.kkt_target, cfg.stol, cfg.mixed_switch = float(kkt_target), float(stol), float(mixed_switch)
         cfg.max_sweeps, cfg.warm_start = int(max_sweeps), int(warm_start)
         cfg.cuda_stream = stream
+        cfg.kkt_abs_target = float(kkt_abs_target)
         h = C.c_void_p()
         check(self.lib.nmf_create(C.byref(cfg), C.byref(h)))
         self.h = h

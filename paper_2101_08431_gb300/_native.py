@@ -16,7 +16,7 @@ NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ECUDA, NMF_ENOTCONV, NMF_ETIMEOUT, NMF_ECAPA
     NMF_ENUMERIC, NMF_ESTATE = range(9)
 NMF_PREC_FP64, NMF_PREC_MIXED = 0, 1
 NMF_DTYPE_F64, NMF_DTYPE_F32 = 0, 1
-NMF_WARM_COLD, NMF_WARM_PREV = 0, 1
+NMF_WARM_COLD, NMF_WARM_PREV, NMF_WARM_CHAIN = 0, 1, 2
 
 # every symbol declared in include/nmf.h
 EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns", "nmf_num_columns",
@@ -40,7 +40,8 @@ _NON_STATUS = ("nmf_config_init", "nmf_num_columns", "nmf_shard_buffer_len", "nm
 class nmf_config(C.Structure):
     _fields_ = [("n", C.c_int64), ("m_capacity", C.c_int64), ("k", C.c_int32), ("prec", C.c_int32),
                 ("stol", C.c_double), ("kkt_target", C.c_double), ("mixed_switch", C.c_double),
-                ("max_sweeps", C.c_int32), ("warm_start", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("max_sweeps", C.c_int32), ("warm_start", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("kkt_abs_target", C.c_double)]
 
 
 class nmf_stats(C.Structure):
@@ -48,7 +49,7 @@ class nmf_stats(C.Structure):
                 ("fp64_sweeps", C.c_int32), ("f", C.c_double), ("kkt_abs", C.c_double),
                 ("kkt_rel", C.c_double), ("step_rel", C.c_double), ("changed_cols", C.c_int64),
                 ("changed_rows", C.c_int64), ("nnls_notconv", C.c_int64), ("measured_iter", C.c_int32),
-                ("pad", C.c_int32)]
+                ("entering_steps", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}

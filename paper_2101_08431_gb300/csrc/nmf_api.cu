@@ -306,6 +306,8 @@ bool make_plan(const nmf_handle* h, int var, YPlan* L) {
   }
   if (C > 8) return false;
   int Q = std::max(1, std::min(h->nsm / C, std::max(h->m, 1)));
+  // the chain warm start runs the whole window in order on one cluster
+  if (h->cfg.warm_start == NMF_WARM_CHAIN && h->k <= 8) Q = 1;
   const int cpc = (std::max(h->m, 1) + Q - 1) / Q;
   const int ntiles = (cpc + K.TJ - 1) / K.TJ;
   const size_t stage = (size_t)K.TJ * R * K.tm_size;
@@ -370,10 +372,12 @@ Problem make_problem(const nmf_handle* h, int var) {
   p.Xd32[1] = h->dXd32[1];
   p.inc = var == VAR_INC ? 1 : 0;
   p.record_refs = 0;
-  p.warm = h->cfg.warm_start != NMF_WARM_COLD;
+  p.tab_global = 0;
+  p.warm = h->cfg.warm_start;   // 0 cold, 1 previous sweep, 2 chain
   p.fp64_pass = var != VAR_F32;
   const bool final_phase = !(h->store_f32 && var == VAR_F32);
   p.kkt_target = final_phase ? h->cfg.kkt_target : 0.0;
+  p.kkt_abs_target = final_phase ? h->cfg.kkt_abs_target : 0.0;
   p.stol = final_phase ? h->cfg.stol : 0.0;
   return p;
 }
@@ -538,6 +542,7 @@ void fill_stats(const nmf_handle* h, int measured, int sweeps, int fp64_sweeps, 
   out->changed_cols = (int64_t)r[ST_CHANGED_COLS];
   out->changed_rows = (int64_t)r[ST_CHANGED_ROWS];
   out->nnls_notconv = (int64_t)r[ST_NOTCONV];
+  out->entering_steps = (int32_t)r[ST_ENTER];
 }
 
 template <typename T>
@@ -620,7 +625,8 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   *out = nullptr;
   const int k = cfg->k;
   if (cfg->n < 1 || cfg->n > (1 << 20) || cfg->m_capacity < 1 || cfg->m_capacity > (1 << 24) ||
-      !((k >= 1 && k <= 8) || k == 16) || (cfg->prec != NMF_PREC_FP64 && cfg->prec != NMF_PREC_MIXED))
+      !((k >= 1 && k <= 8) || k == 16) || (cfg->prec != NMF_PREC_FP64 && cfg->prec != NMF_PREC_MIXED) ||
+      cfg->warm_start < NMF_WARM_COLD || cfg->warm_start > NMF_WARM_CHAIN)
     return NMF_EINVAL;
   nmf_handle* h = new (std::nothrow) nmf_handle();
   if (!h) return NMF_ENOMEM;
@@ -946,6 +952,7 @@ nmf_status nmf_shard_y_half(nmf_handle* h, double* sum_buf, double* max_buf, int
     return fail(h, NMF_EINVAL, "no launch plan for this shape");
   }
   Problem p = make_problem(h, var);
+  p.tab_global = 0;     // H is formed from the reduced buffers by the X half
   CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
   if (use_tc) CUDA_TRY(h, tc16_launch(p, MODE_SWEEP, T, h->stream));
   else CUDA_TRY(h, h->ks[var].ypass(p, MODE_SWEEP, L, h->stream));
@@ -986,6 +993,7 @@ nmf_status nmf_shard_x_half(nmf_handle* h, const double* sum_buf, const double* 
   p.Ppart = P;
   p.Hpart = H;
   p.Yterms = Yt;
+  p.tab_global = 0;     // the row blocks form H's table from the reduced H
   p.fp64_pass = h->shard_var != VAR_F32;
   CUDA_TRY(h, h->ks[var_x].xpass(p, MODE_SWEEP, 1, h->nxblk, h->stream));
   h->launches += 2;
@@ -1137,7 +1145,7 @@ struct SaveHeader {
   uint32_t version, devstate_bytes;
   int64_t n, ld, mcap, m;
   int32_t k, prec, max_sweeps, warm_start;
-  double stol, kkt_target, mixed_switch;
+  double stol, kkt_target, mixed_switch, kkt_abs_target;
   int32_t factors_set, phase, forced_mode, chunks_since_best;
   double best_rel;
 };
@@ -1190,6 +1198,7 @@ nmf_status nmf_save(nmf_handle* h, const char* path) {
   hd.warm_start = h->cfg.warm_start;
   hd.stol = h->cfg.stol;
   hd.kkt_target = h->cfg.kkt_target;
+  hd.kkt_abs_target = h->cfg.kkt_abs_target;
   hd.mixed_switch = h->cfg.mixed_switch;
   hd.factors_set = h->factors_set ? 1 : 0;
   hd.phase = h->phase;
@@ -1274,6 +1283,7 @@ nmf_status nmf_load(const char* path, void* cuda_stream, nmf_handle** out) {
   cfg.prec = hd.prec;
   cfg.stol = hd.stol;
   cfg.kkt_target = hd.kkt_target;
+  cfg.kkt_abs_target = hd.kkt_abs_target;
   cfg.mixed_switch = hd.mixed_switch;
   cfg.max_sweeps = hd.max_sweeps;
   cfg.warm_start = hd.warm_start;

@@ -24,7 +24,8 @@
 // yval (staging of X from its stored copies, of y from FP64), zero, vzero,
 // madd, add, shfl_xor, to_double, to_p, to_r, radd, rshfl_xor, r_to_double,
 // EPS (the epsilon of the NNLS entering tolerance for sweeps computed with
-// this policy) and INC (the incremental form).
+// this policy), INC (the incremental form) and REFINE (one step of iterative
+// refinement in the table-driven column solves).
 #pragma once
 
 #include "nmf_common.cuh"
@@ -84,6 +85,7 @@ struct ArF32 {
   using P = float;
   static constexpr bool XD = false;   // X is staged from its FP32 copy
   static constexpr bool INC = false;
+  static constexpr bool REFINE = false;   // B is FP32-accurate: no refinement step in the solves
   static constexpr bool PACC_SMEM = false;   // P accumulators in registers
   // the FP64 column solves take the FP64 entering tolerance: a coarser one
   // leaves out variables whose small gradient hides a large value where G is
@@ -112,6 +114,7 @@ struct ArF64 {
   using P = double;
   static constexpr bool XD = true;
   static constexpr bool INC = false;
+  static constexpr bool REFINE = true;    // one refinement step of the table solve
   static constexpr bool PACC_SMEM = false;
   static constexpr double EPS = 2.220446049250313e-16;
   using R = double;
@@ -137,6 +140,7 @@ struct ArDF {
   using P = DF;   // partials stay double-float: no FP64 instruction in the epilogue
   static constexpr bool XD = true;
   static constexpr bool INC = false;
+  static constexpr bool REFINE = true;
   static constexpr double EPS = 5.684341886080802e-14;   // 2^-44
   // the P accumulators (two words each) live in shared memory, so that a
   // CTA holds as many rows as in the FP32 pass (no cluster exchange)
@@ -177,6 +181,9 @@ struct ArInc {
   // FP64-class solves (one refinement step): B and P are FP64-accurate
   static constexpr bool XD = true;
   static constexpr bool INC = true;
+  // the FP64 table solve's own error (~2^-53 cond) is far below that of B
+  // (~2^-44 cond): no refinement step
+  static constexpr bool REFINE = false;
   static constexpr bool PACC_SMEM = false;
   static constexpr double EPS = 5.684341886080802e-14;   // 2^-44, as the compensated pass
   using R = DF;

@@ -182,6 +182,9 @@ nmf_status build_plan(nmf_batch* b) {
       return bfail(b, NMF_EINVAL, "no problem view");
     for (int v = 0; v < 2; ++v) {
       bp.pv[v].tab_global = 1;
+      // the chain warm start is a one-problem form: batched items start
+      // every column from its previous-sweep solution
+      if (bp.pv[v].warm == NMF_WARM_CHAIN) bp.pv[v].warm = NMF_WARM_PREV;
       bp.pv[v].auto_mixed = b->force_var < 0 ? 1 : 0;
       bp.pv[v].stall_sweeps = STALL_SWEEPS;
       bp.pv[v].mixed_switch = b->cfg[j].mixed_switch;
@@ -189,6 +192,7 @@ nmf_status build_plan(nmf_batch* b) {
     if (b->force_var >= 0) {
       // a fixed pass: every sweep may stop on the targets
       bp.pv[0].kkt_target = bp.pv[1].kkt_target;
+      bp.pv[0].kkt_abs_target = bp.pv[1].kkt_abs_target;
       bp.pv[0].stol = bp.pv[1].stol;
     }
     bp.S[0] = batch_stages(*k0, R, Q, hi.m, b->stage_cap, budget);

@@ -72,29 +72,6 @@ __device__ __forceinline__ void batch_wait(const unsigned* ctr, unsigned target,
   __threadfence();
 }
 
-// H stage of problem p after its M pass (k <= 8): H = Y Y^T from the Q
-// cluster partials (the same fixed-order tree as the row pass), and its
-// subset table, into the problem's global buffers; every row block of the
-// sweep then reads them instead of forming them itself.  All 512 threads.
-// The table is in the value type of the sweep's row solves (NV: FP32 for the
-// FP32 pass), stored in the problem's table buffer.
-template <int K, typename NV>
-__device__ void batch_h_stage(const Problem& p, int Q, unsigned char* smem_raw) {
-  double* H = reinterpret_cast<double*>(smem_raw);
-  NV* Hn = reinterpret_cast<NV*>(smem_raw + 2048);
-  tree_sum<512>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
-  __syncthreads();
-  for (int e = threadIdx.x; e < K * K; e += 512) {
-    p.Hg[e] = H[e];
-    Hn[e] = (NV)H[e];
-  }
-  __syncthreads();
-  NnlsSolver<K> solver;
-  solver.init(H, 2.220446049250313e-16);
-  build_subset_table_lanes_v<K, NV>(Hn, (NV)solver.pivot_min, reinterpret_cast<NV*>(p.Htab), p.Hok, 0, 512,
-                                    [] { __syncthreads(); });
-}
-
 template <int K>
 __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -143,8 +120,8 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs a) {
         __syncthreads();
         if constexpr (HS != 0) {
           if (s_item[2]) {
-            if (var == 0) batch_h_stage<K, typename XSmem<float, K>::SV>(bp.pv[0], bp.Q, smem_raw);
-            else batch_h_stage<K, double>(bp.pv[0], bp.Q, smem_raw);
+            if (var == 0) h_stage<K, typename XSmem<float, K>::SV>(bp.pv[0], bp.Q, smem_raw);
+            else h_stage<K, double>(bp.pv[0], bp.Q, smem_raw);
             __syncthreads();
             if (threadIdx.x == 0) {
               __threadfence();

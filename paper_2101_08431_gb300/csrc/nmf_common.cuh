@@ -17,7 +17,7 @@ namespace cg = cooperative_groups;
 constexpr int KMAX = 16;           // largest rank the kernels are built for
 constexpr int STAT_CAP = 64;       // per-iterate statistics ring
 constexpr int NSTAT = 16;          // doubles per statistics record
-constexpr int NYT = 10;            // KKT / objective terms of the Y half (per cluster)
+constexpr int NYT = 11;            // KKT / objective terms of the Y half (per cluster)
 constexpr int NXT = 10;            // terms of the X half (per row block)
 constexpr int CACHE_N = 8;         // inverse-cache entries per CTA
 constexpr long long SPIN_LIMIT = 1ll << 26;   // bounded waits (about a second)
@@ -30,14 +30,14 @@ constexpr unsigned ERR_CONFIG = 4u;
 // Y-half terms, for the iterate (X_t, Y_t) entering a sweep:
 //   graY_j = G y_j - b_j with b_j = X_t^T M_{:,j} and G = X_t^T X_t
 enum YTerm { YT_NEG = 0, YT_COMP, YT_BNORM2, YT_BY, YT_YGY, YT_YMAX, YT_YNORM2, YT_DY2,
-             YT_CHANGED, YT_NOTCONV };
+             YT_CHANGED, YT_NOTCONV, YT_ENTER };
 // X-half terms, for the iterate (X_{t+1}, Y_{t+1}) leaving a sweep:
 //   graX_i = H x_i - P_i with H = Y Y^T and P = M Y^T
 enum XTerm { XT_NEG = 0, XT_COMP, XT_PNORM2, XT_XMAX, XT_XNORM2, XT_DX2, XT_XP,
              XT_CHANGED, XT_NOTCONV, XT_VALID };
 // statistics record of iterate t
 enum Stat { ST_ITER = 0, ST_F, ST_EABS, ST_REL, ST_STEP, ST_NEG, ST_COMP, ST_SG, ST_XYMAX,
-            ST_CHANGED_COLS, ST_CHANGED_ROWS, ST_NOTCONV, ST_FP64, ST_MSQ, ST_VALID };
+            ST_CHANGED_COLS, ST_CHANGED_ROWS, ST_NOTCONV, ST_FP64, ST_MSQ, ST_VALID, ST_ENTER };
 
 // Device-resident control block of one problem.
 struct DevState {
@@ -95,8 +95,10 @@ struct Problem {
   double* Xpart;          // [nxblk][k*k + NXT]
   DevState* st;
   double kkt_target;      // <= 0 disables
+  double kkt_abs_target;  // <= 0 disables
   double stol;            // <= 0 disables
-  int warm;               // 0 cold, 1 previous sweep (new columns are seeded at append)
+  int warm;               // 0 cold, 1 previous sweep (new columns are seeded at append),
+                          // 2 chain: column j from column j - 1's new solution
   int fp64_pass;          // 1 when this sweep's M pass runs in FP64
   // device-driven mixed schedule (batched form): FP32 passes until the
   // relative KKT reaches mixed_switch or has not improved by 2% for

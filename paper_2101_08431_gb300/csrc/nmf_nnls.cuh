@@ -625,7 +625,7 @@ __device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, in
 template <int K, typename V = double>
 __device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const V* tab, const int* ok,
                                                const V (&grow)[K], V gmax, V eps, V b, V& y, bool warm,
-                                               bool active, bool refine, uint32_t* mask) {
+                                               bool active, bool refine, uint32_t* mask, int* entered = nullptr) {
   using O = VOps<V>;
   constexpr int KP = LaneGroup<K>::KP;
   const bool comp = active && g.a < K;
@@ -637,7 +637,7 @@ __device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const V* t
   uint32_t P = g.bits(ypos);
   if (!ypos) y = V(0);
   uint32_t blocked = 0;
-  int t_in = -1, status = active ? 1 : 0;
+  int t_in = -1, status = active ? 1 : 0, n_in = 0;
   bool done = !active;
 #pragma unroll 1
   for (int it = 0; it < 6 * K + 12; ++it) {
@@ -727,11 +727,13 @@ __device__ __forceinline__ int lane_table_nnls(const LaneGroup<K>& g, const V* t
           const int t = __ffs(at) - 1;
           P |= 1u << t;
           t_in = t;
+          ++n_in;
         }
       }
     }
   }
   *mask = g.bits(comp && vpos(y));
+  if (entered) *entered = n_in;
   return status;
 }
 

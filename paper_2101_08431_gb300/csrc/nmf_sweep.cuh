@@ -401,6 +401,9 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         }
         om_nx = p.ymask[cur][ph_nx];
       }
+      // chain warm start: the last solved column's new y (component g.a)
+      double chain_y = 0.0;
+      bool chain_started = false;
       if constexpr (Tr::LOCAL_TAB) {
         if (mode == MODE_SWEEP && !gglob) {
           if constexpr (F32NN)
@@ -453,38 +456,68 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
         double yn = yo;
         if (mode == MODE_SWEEP) {
           uint32_t msk = 0;
-          NV ynv = (NV)yn;
-          int stt = lane_table_nnls<K, NV>(g, gtab, gok, grown, (NV)solver.gmax, (NV)AR::EPS, (NV)b, ynv,
-                                           p.warm != 0, active, AR::XD, &msk);
-          yn = (double)ynv;
-          if (__any_sync(0xffffffffu, stt < 0)) {
-            // a degenerate table entry: the group's first lane solves the
-            // column with the incremental solver, then scatters the result
-            double bb[K], yy[K];
+          int stt = 0, nin = 0;
+          // one warm-started solve of the columns whose lanes have `act` set,
+          // from ystart; a degenerate table entry falls back to the
+          // incremental solver on the group's first lane
+          auto solve_cols = [&](double ystart, bool act, double& yo_out, uint32_t& msk_out, int& st_out,
+                                int& nin_out) {
+            NV ynv = (NV)ystart;
+            int ss = lane_table_nnls<K, NV>(g, gtab, gok, grown, (NV)solver.gmax, (NV)AR::EPS, (NV)b, ynv,
+                                            p.warm != 0, act, AR::REFINE, &msk_out, &nin_out);
+            yo_out = (double)ynv;
+            if (__any_sync(0xffffffffu, ss < 0)) {
+              double bb[K], yy[K];
 #pragma unroll
-            for (int c = 0; c < K; ++c) {
-              bb[c] = g.from(b, c);
-              yy[c] = g.from(yo, c);
-            }
-            uint32_t m2 = 0;
-            int s2 = 0;
-            if (stt < 0 && g.a == 0) s2 = solver.solve(Ascr, bb, yy, p.warm != 0, nullptr, &m2);
+              for (int c = 0; c < K; ++c) {
+                bb[c] = g.from(b, c);
+                yy[c] = g.from(ystart, c);
+              }
+              uint32_t m2 = 0;
+              int s2 = 0;
+              if (ss < 0 && g.a == 0) s2 = solver.solve(Ascr, bb, yy, p.warm != 0, nullptr, &m2);
 #pragma unroll
-            for (int c = 0; c < K; ++c) {
-              const double v = __shfl_sync(0xffffffffu, yy[c], g.base);
-              if (stt < 0 && g.a == c) yn = v;
+              for (int c = 0; c < K; ++c) {
+                const double v = __shfl_sync(0xffffffffu, yy[c], g.base);
+                if (ss < 0 && g.a == c) yo_out = v;
+              }
+              const uint32_t mm = __shfl_sync(0xffffffffu, m2, g.base);
+              const int s3 = __shfl_sync(0xffffffffu, s2, g.base);
+              if (ss < 0) {
+                msk_out = mm;
+                ss = s3;
+              }
             }
-            const uint32_t mm = __shfl_sync(0xffffffffu, m2, g.base);
-            const int ss = __shfl_sync(0xffffffffu, s2, g.base);
-            if (stt < 0) {
-              msk = mm;
-              stt = ss;
+            st_out = ss;
+          };
+          if (p.warm == 2) {
+            // the paper's chain (Sec. 2): the tile's columns one after
+            // another, each starting from the previous column's new solution
+            // (the CTA's first column from its own previous-sweep solution)
+            for (int sl = 0; sl < TJ; ++sl) {
+              if (sl >= tj) break;                       // uniform: tj is the same on every lane
+              const double ystart = chain_started ? chain_y : yo;
+              double ys = 0.0;
+              uint32_t ms = 0;
+              int sts = 0, ns = 0;
+              solve_cols(ystart, active && jj == sl, ys, ms, sts, ns);
+              if (jj == sl) {
+                yn = ys;
+                msk = ms;
+                stt = sts;
+                nin = ns;
+              }
+              chain_y = __shfl_sync(0xffffffffu, ys, sl * LaneGroup<K>::KP + (ca ? g.a : 0));
+              chain_started = true;
             }
+          } else {
+            solve_cols(yo, active, yn, msk, stt, nin);
           }
           if (comp) acc_t[YT_DY2] = fmad(yn - yo, yn - yo, acc_t[YT_DY2]);
           if (active && g.a == 0) {
             acc_t[YT_CHANGED] += (old_mask != msk) ? 1.0 : 0.0;
             acc_t[YT_NOTCONV] += (double)stt;
+            acc_t[YT_ENTER] += (double)nin;
           }
           if (crank == 0 && active) {
             if (ca) p.Y[nxt][(size_t)phys * K + g.a] = yn;
@@ -636,13 +669,6 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
   if (C > 1) cluster.sync();
 }
 
-template <typename TM, typename AR, int K>
-__global__ void __launch_bounds__(512, 1)
-    ypass_kernel(Problem p, int mode, int S, int C, int R, int Q) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  ypass_body<TM, AR, K>(p, mode, S, C, R, Q, (int)blockIdx.x / C, smem_raw);
-}
-
 // ---------------------------------------------------------------------------
 // Statistics record of iterate t (Sec. 5.1 KKT error with r = max(graX, 0),
 // s = max(graY, 0), 2-norms; f from the Grams) from the Y-half terms (this
@@ -687,6 +713,7 @@ __device__ inline void combine_stats_warp(const double* yterm, const double* xte
   out[ST_XYMAX] = xymax;
   out[ST_CHANGED_COLS] = yterm[YT_CHANGED];
   out[ST_NOTCONV] = yterm[YT_NOTCONV];
+  out[ST_ENTER] = yterm[YT_ENTER];
   out[ST_FP64] = fp64;
   out[ST_MSQ] = msq;
   out[ST_VALID] = xterm[XT_VALID];
@@ -1211,7 +1238,8 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
         }
         if (rel <= p.mixed_switch || st->since_best >= p.stall_sweeps) st->pass_var = VAR_DF;
       }
-      const bool kkt_ok = p.kkt_target > 0.0 && rec[ST_VALID] > 0.0 && rec[ST_REL] <= p.kkt_target;
+      const bool kkt_ok = rec[ST_VALID] > 0.0 && ((p.kkt_target > 0.0 && rec[ST_REL] <= p.kkt_target) ||
+                                                  (p.kkt_abs_target > 0.0 && rec[ST_EABS] <= p.kkt_abs_target));
       const bool step_ok = p.stol > 0.0 && rec[ST_STEP] >= 0.0 && rec[ST_STEP] <= p.stol;
       if (kkt_ok) {
         st->done = 1;
@@ -1234,6 +1262,41 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       st_release_u32(tail_done, tail_value);
     }
   }
+}
+
+// H stage of problem p after its M pass (k <= 8): H = Y Y^T from the Q
+// cluster partials (the same fixed-order tree as the row pass), and its
+// subset table, into the problem's global buffers; every row block of the
+// sweep then reads them instead of forming them itself.  All 512 threads of
+// the batch item that completes the problem's M pass.  (The one-problem
+// sweep does not use it: its row blocks form the table while their other
+// warps sum the P partials, which hides it, whereas a stage at the end of
+// the M pass adds its FP64 chains to the sweep's critical path.)
+// The table is in the value type of the sweep's row solves (NV: FP32 for the
+// FP32 pass), stored in the problem's table buffer.
+template <int K, typename NV>
+__device__ void h_stage(const Problem& p, int Q, unsigned char* smem_raw) {
+  double* H = reinterpret_cast<double*>(smem_raw);
+  NV* Hn = reinterpret_cast<NV*>(smem_raw + 2048);
+  tree_sum<512>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += 512) {
+    p.Hg[e] = H[e];
+    Hn[e] = (NV)H[e];
+  }
+  __syncthreads();
+  NnlsSolver<K> solver;
+  solver.init(H, 2.220446049250313e-16);
+  build_subset_table_lanes_v<K, NV>(Hn, (NV)solver.pivot_min, reinterpret_cast<NV*>(p.Htab), p.Hok, 0, 512,
+                                    [] { __syncthreads(); });
+}
+
+template <typename TM, typename AR, int K>
+__global__ void __launch_bounds__(512, 1)
+    ypass_kernel(Problem p, int mode, int S, int C, int R, int Q) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (p.st->done) return;                     // uniform: written by an earlier launch
+  ypass_body<TM, AR, K>(p, mode, S, C, R, Q, (int)blockIdx.x / C, smem_raw);
 }
 
 template <typename TA, int K>

@@ -184,6 +184,45 @@ def test_incremental_chunk_tracks_the_oracle(n, m, k):
     assert _masks_agree(Yi, ymi, Yo, 1e-9)
 
 
+def test_chain_warm_start_takes_the_oracle_chain_steps():
+    """Sec. 2's chain, the paper's own warm start: column j starts from column
+    j - 1's new solution, one column after another.  On the oracle's chain
+    state (PDF-like 400 x 200 x 4 after 100 sweeps) one GPU sweep with
+    NMF_WARM_CHAIN gives the oracle's sweep (unique solutions, 1e-9 per
+    column and row), and its column solves take the entering steps of the
+    oracle's warm-started chain -- a small fraction of the cold solver's,
+    which the cold GPU sweep matches."""
+    S = _lib()
+    from paper_2101_08431_gb300 import NMF_WARM_CHAIN, NMF_WARM_COLD
+    n, m, k = 400, 200, 4
+    M, _, _ = synth.pdf_like(n, m, k, noise=1e-3, relative=True, seed=1)
+    X, Y = synth.init_factors(n, m, k, seed=1)
+    X, Y, _, _, _, _, st = oracle.anls(M, X, Y, max_sweeps=100)
+    X, Y = np.ascontiguousarray(X), np.ascontiguousarray(Y)
+    G, B = X.T @ X, X.T @ M
+    cold = chain = 0
+    prev = Y[:, 0]                       # column 0 starts from its previous-sweep solution
+    for j in range(m):
+        _, _, oc, _ = oracle.nnls(G, B[:, j])
+        yw, _, ow, _, _ = oracle.nnls_warm(G, B[:, j], prev)
+        cold += oc
+        chain += ow
+        prev = yw
+    Xo, Yo, _, _, _ = oracle.sweep(M, X, Y)
+    steps = {}
+    for ws in (NMF_WARM_CHAIN, NMF_WARM_COLD):
+        with _handle(S, M, X, Y, PREC_FP64, warm_start=ws) as h:
+            stt = h.sweep(1)
+            Xg, Yg, _, _ = h.get_factors()
+        steps[ws] = stt["entering_steps"]
+        assert _rel_y(Yg, Yo) <= 1e-9 and _rel_x(Xg, Xo) <= 1e-9
+    print("entering steps: GPU chain %d, oracle chain %d; GPU cold %d, oracle cold %d"
+          % (steps[NMF_WARM_CHAIN], chain, steps[NMF_WARM_COLD], cold))
+    assert abs(steps[NMF_WARM_CHAIN] - chain) <= 2
+    assert abs(steps[NMF_WARM_COLD] - cold) <= 2
+    assert steps[NMF_WARM_CHAIN] <= 0.25 * steps[NMF_WARM_COLD]
+
+
 def test_ten_fp64_sweeps_track_the_oracle():
     S = _lib()
     M, X, Y = _state(1200, 400, 4, seed=7, warm_sweeps=30)
@@ -245,6 +284,28 @@ def test_run_to_target_matches_oracle_fp64(case):
     assert oracle.objective(M, Xg, Yg) == pytest.approx(tr[-1, 0], rel=1e-8)
     np.testing.assert_array_equal(ymg, ymo)
     np.testing.assert_allclose(Xg @ Yg, Xo @ Yo, rtol=0, atol=1e-6 * np.abs(M).max())
+
+
+def test_absolute_kkt_stop_matches_the_oracle_trace():
+    """kkt_abs_target: the paper's own stopping rule, absolute E <= 1e-6
+    (Sec. 5.1), on its Sec. 5.4 synthetic recipe at (2000, 50, 3).  The FP64
+    form stops at the first iterate of the oracle's trajectory whose E is
+    below the target, and the oracle certifies the returned iterate."""
+    S = _lib()
+    n, m, k = 2000, 50, 3
+    M, _, _ = synth.paper_uniform(n, m, k, sigma=0.1, seed=0)
+    X, Y = synth.init_factors(n, m, k, seed=0)
+    _, _, _, _, _, tr, st = oracle.anls(M, X, Y, max_sweeps=2700, want_trace=True)
+    hit = int(np.nonzero(tr[:, 1] <= 1e-6)[0][0])
+    h = S(n, k, m, prec=PREC_FP64, kkt_target=0.0, kkt_abs_target=1e-6, max_sweeps=20000)
+    h.append_columns(np.asfortranarray(M))
+    h.set_factors(X, Y)
+    stt = h.sweep(0)
+    Xg, Yg, _, _ = h.get_factors()
+    h.close()
+    assert stt["converged"] == 1 and stt["kkt_abs"] <= 1e-6
+    assert abs(stt["sweeps"] - (hit + 1)) <= 2, (stt["sweeps"], hit)
+    assert oracle.kkt(M, Xg, Yg)["E_abs"] <= 1.001e-6
 
 
 def test_mixed_run_to_target_beats_fp32_floor():
