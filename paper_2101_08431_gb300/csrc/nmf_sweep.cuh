@@ -833,9 +833,12 @@ struct XSmem {
   using SV = typename std::conditional<F32NN, float, double>::type;
   // k = 16: value type of the 16-lane row solves
   using V16 = double;
-  // Lawson-Hanson tolerance constant of the FP64 row solves (incremental
-  // sweeps use 2^-44, as the compensated pass)
-  static constexpr double EPS = 2.220446049250313e-16;
+  // Lawson-Hanson tolerance constant of the FP64 row solves: 2^-52, but 2^-23
+  // at rank 16 with FP32 partials (the tensor-core pass: its P carries ~1e-5,
+  // and entering decisions below that level would follow the rounding of P);
+  // incremental sweeps use 2^-44, as the compensated pass
+  static constexpr double EPS =
+      (std::is_same<TA, float>::value && K > 8) ? 1.1920928955078125e-07 : 2.220446049250313e-16;
   struct Small {
     double H[K * K];
     double Gs[K * K];

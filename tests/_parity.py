@@ -100,7 +100,7 @@ PASS_UNITS = {
     # split-BF16 products (2^-15, tests/test_split_bf16_bound.py), FP32 sums;
     # FP32 column solves (kappa, eps), FP64 row solves (kappa_x, eps_x)
     "tc16": dict(u=lambda L: 2.0 ** -15 + 2.0 * (L - 1) * 2.0 ** -24, kappa=2.0 ** -18, kappa_x=2.0 ** -40,
-                 eps=2.0 ** -23, eps_x=2.0 ** -52),
+                 eps=2.0 ** -23, eps_x=2.0 ** -23),
 }
 
 
