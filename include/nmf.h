@@ -118,7 +118,8 @@ void nmf_config_init(nmf_config *cfg);
 /* Create a handle for one problem of n rows, rank k and up to m_capacity
  * resident columns (Sec. 1's streaming setting).  Allocates all device
  * memory up front; no allocation happens in later calls except
- * nmf_append_columns' staging of host data.  Errors: NMF_EINVAL for n < 1,
+ * nmf_append_columns' staging of host data and the work memory of the
+ * stage-2 calls (nmf_ipm, nmf_ipm_direction) and of the first shard call.  Errors: NMF_EINVAL for n < 1,
  * k outside 1..8 and 16, m_capacity < 1 or n beyond the kernels' row limit
  * (16384 rows FP32, 8192 FP64); NMF_ENOMEM; NMF_ECUDA.
  * Ranks: the passive-set masks would hold k <= 32, but the kernels are built
@@ -268,6 +269,34 @@ int64_t nmf_shard_buffer_len(int64_t n, int32_t k);
 nmf_status nmf_shard_y_half(nmf_handle *h, double *sum_buf, double *max_buf, int32_t on_device);
 nmf_status nmf_shard_x_half(nmf_handle *h, const double *sum_buf, const double *max_buf, int32_t on_device,
                             nmf_stats *stats);
+
+/* Stage 2 of the two-stage method (Alg. "alg:fast", Sec. 3-4) on the GPU, in
+ * FP64, from the handle's current iterate (its resident window): the
+ * transition of Sec. 4 (eqs. "upxy", "rho0", "rs", "mu", "rho" with
+ * rho = eps_tol), then the outer loop on mu with the inner Newton loop of the
+ * primal-dual interior point method -- fraction to the boundary (tau = 0.9),
+ * Armijo backtracking on the barrier merit function (eq. "eqn:armijo",
+ * eta = 0.5, at most 60 halvings), the predictor-based sigma (eqs.
+ * "eqn:muaff", "eqn:mu") and the switch to the full Hessian at
+ * sigma <= 0.01 when it gives a descent direction -- until the KKT error
+ * E(.;0) <= eps_tol or max_newton Newton steps.  Each direction is formed as
+ * in Sec. 3.2 (block Cholesky of R1, W = Cb P^-1, the mk x mk Schur matrix
+ * and its dense Cholesky).  The result becomes the handle's iterate (primed as
+ * by nmf_set_factors).  stats (NULL or 7 doubles): E(.;0) at exit, f, Newton
+ * steps, outer steps, final mu, steps that used the full Hessian, Armijo
+ * failures.  Work memory is allocated for the call: 8 (m k (n k + m k) +
+ * n k^2 + ...) bytes; NMF_ECAPACITY when m k > 4096 or n k m k > 2^27.
+ * Returns NMF_ENOTCONV at the Newton cap (for n != m the printed method can
+ * drift along the scaling orbit of the factorization and end there),
+ * NMF_ENUMERIC if a factorisation is not positive definite, NMF_ESTATE before
+ * factors are set.
+ * nmf_ipm_direction: one direction of eq. "eqn:equation" at the handle's
+ * iterate for duals r (n x k, like X) and s (k x m, like Y), barrier mu >= 0,
+ * regularisation rho >= 0, full = 1 for the full Hessian blocks C (else the
+ * Gauss-Newton blocks): dx, dy, dr, ds in the layouts of X, Y, X, Y. */
+nmf_status nmf_ipm(nmf_handle *h, double eps_tol, int32_t max_newton, double *stats);
+nmf_status nmf_ipm_direction(nmf_handle *h, const double *r, const double *s, double mu, double rho,
+                             int32_t full, double *dx, double *dy, double *dr, double *ds, int32_t on_device);
 
 /* The accumulated device time (ms) of the M passes and of the row passes
  * of one pass variant since nmf_set_timing(h, 1), and how many sweeps ran

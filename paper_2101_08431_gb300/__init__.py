@@ -161,6 +161,33 @@ class StreamingNMF:
                                         C.byref(st)), self.h)
         return st.as_dict()
 
+    # -- stage 2 (Sec. 3-4) --------------------------------------------------------
+    IPM_STATS = ("E0", "f", "newton", "outer", "mu", "full_hessian_steps", "armijo_failures")
+
+    def ipm(self, eps_tol=1e-6, max_newton=500, allow_notconv=False):
+        """Stage 2 from the current iterate; returns its statistics (the
+        result becomes the handle's iterate)."""
+        st = np.zeros(7)
+        s = self.lib.nmf_ipm(self.h, float(eps_tol), int(max_newton), st.ctypes.data_as(C.POINTER(C.c_double)))
+        if not (allow_notconv and s == _native.NMF_ENOTCONV):
+            check(s, self.h)
+        d = dict(zip(self.IPM_STATS, st.tolist()))
+        d["status"] = s
+        return d
+
+    def ipm_direction(self, R, S, mu, rho, full):
+        """One Newton direction of stage 2 at the current iterate for duals
+        R (n x k) and S (k x m): (dX, dY, dR, dS)."""
+        m = self.m
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        S = np.asfortranarray(S, dtype=np.float64)
+        dX, dR = np.zeros((self.n, self.k)), np.zeros((self.n, self.k))
+        dY, dS = np.zeros((self.k, m), order="F"), np.zeros((self.k, m), order="F")
+        ptr = lambda a: C.c_void_p(a.ctypes.data)
+        check(self.lib.nmf_ipm_direction(self.h, ptr(R), ptr(S), float(mu), float(rho), int(bool(full)), ptr(dX),
+                                         ptr(dY), ptr(dR), ptr(dS), 0), self.h)
+        return dX, np.ascontiguousarray(dY), dR, np.ascontiguousarray(dS)
+
     # -- persistence ------------------------------------------------------------
     def save(self, path):
         """Write the handle's window, iterate and sweep state to path."""

@@ -22,7 +22,7 @@ NMF_WARM_COLD, NMF_WARM_PREV, NMF_WARM_CHAIN = 0, 1, 2
 EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns", "nmf_num_columns",
            "nmf_set_factors", "nmf_get_factors", "nmf_sweep", "nmf_set_pass_mode",
            "nmf_objective_kkt", "nmf_status_string", "nmf_last_error", "nmf_launch_count",
-           "nmf_set_timing", "nmf_get_timing", "nmf_get_pass_timing", "nmf_shard_buffer_len", "nmf_shard_y_half", "nmf_shard_x_half", "nmf_save", "nmf_load", "nmf_get_config", "nmf_sweep_noalloc",
+           "nmf_set_timing", "nmf_get_timing", "nmf_get_pass_timing", "nmf_shard_buffer_len", "nmf_shard_y_half", "nmf_shard_x_half", "nmf_ipm", "nmf_ipm_direction", "nmf_save", "nmf_load", "nmf_get_config", "nmf_sweep_noalloc",
            "nmf_batch_create", "nmf_batch_destroy", "nmf_batch_size", "nmf_batch_problem",
            "nmf_batch_append_columns", "nmf_batch_set_factors", "nmf_batch_get_factors",
            "nmf_batch_set_pass_mode", "nmf_batch_set_schedule", "nmf_batch_sweep", "nmf_batch_autotune",
@@ -127,6 +127,9 @@ def load(path: str = LIB_PATH):
     L.nmf_shard_buffer_len.restype = C.c_int64
     L.nmf_shard_y_half.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32]
     L.nmf_shard_x_half.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(nmf_stats)]
+    L.nmf_ipm.argtypes = [H, C.c_double, C.c_int32, C.POINTER(C.c_double)]
+    L.nmf_ipm_direction.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
     L.nmf_save.argtypes = [H, C.c_char_p]
     L.nmf_load.argtypes = [C.c_char_p, C.c_void_p, C.POINTER(H)]
     L.nmf_get_config.argtypes = [H, C.POINTER(nmf_config)]

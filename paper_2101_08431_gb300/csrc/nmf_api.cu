@@ -373,6 +373,10 @@ Problem make_problem(const nmf_handle* h, int var) {
   p.inc = var == VAR_INC ? 1 : 0;
   p.record_refs = 0;
   p.tab_global = 0;
+  // k <= 8: the row pass's last block builds the subset table of the new G
+  // (beside the statistics) for the next M pass, whose NNLS warp would
+  // otherwise build it before its first solve
+  p.gtab_tail = h->k <= 8 ? 1 : 0;
   p.warm = h->cfg.warm_start;   // 0 cold, 1 previous sweep, 2 chain
   p.fp64_pass = var != VAR_F32;
   const bool final_phase = !(h->store_f32 && var == VAR_F32);

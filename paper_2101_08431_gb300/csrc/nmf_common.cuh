@@ -88,6 +88,7 @@ struct Problem {
   int* Hok;
   int tab_global;         // 1: the tables of G and H are built once per sweep into global
                           // memory (G by the row pass's tail, H by the batch's H stage)
+  int gtab_tail;          // 1: the table of G alone is built by the row pass's tail
   const double* colsq;    // ||M_{:,j}||^2 per physical column
   void* Ppart;            // [Q][ld][k] partial M Y^T (accumulate type)
   double* Hpart;          // [Q][k][k]

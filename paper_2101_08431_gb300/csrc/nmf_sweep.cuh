@@ -77,7 +77,10 @@ struct YSmem {
     double yt[Tr::TJ][NYT];            // per-column-lane KKT / objective terms (k > 8)
     double lt[32][NYT];                // per-lane KKT / objective terms (k <= 8)
     uint32_t samples[CACHE_N];
-    InvCache<K> cache;                 // k > 8 only (no subset table)
+    union {
+      InvCache<K> cache;               // k > 8 only (no subset table)
+      double lh[32][K];                // k <= 8: per-lane accumulators of H rows
+    };
     // subset table of G built by the NNLS warp, in the value type of the
     // solve: FP32 for the FP32 pass, FP64 otherwise; Gn: G in that type
     typename Tr::NV gtab[Tr::LOCAL_TAB ? (1 << K) * K * K : 1];
@@ -306,6 +309,28 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
     }
 
     // ---- epilogue: partials of this cluster
+    if constexpr (TABLE) {
+      // the NNLS warp's per-lane KKT terms and H accumulators, reduced in
+      // the fixed butterfly orders of one warp each (a term over the 32
+      // lanes; a column of H over the lane groups' column slots), one item
+      // per compute warp
+      constexpr int KP = LaneGroup<K>::KP;
+      for (int item = warp; item < NYT + K; item += NCW) {
+        if (item < NYT) {
+          const double v0 = sm.lt[lane][item];
+          const double v = (item == YT_YMAX) ? warp_max(v0) : warp_sum(v0);
+          if (lane == 0) sm.yt[0][item] = v;
+        } else {
+          const int c = item - NYT;
+          double v = sm.lh[lane][c];
+#pragma unroll
+          for (int o = KP; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          const int a = lane & (KP - 1);
+          if (lane < KP && a < K) sm.Hacc[a * K + c] = v;
+        }
+      }
+      named_sync(1, TC);
+    }
     typename AR::P* Pp = static_cast<typename AR::P*>(p.Ppart);
     if (mode != MODE_KKT) {
 #pragma unroll
@@ -376,7 +401,7 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
       // k = 7, 8 always, k <= 6 when the row pass's tail has built it: the
       // table of G in global memory; otherwise this warp builds it below
       // (FP32 solves: always this warp's own FP32 table)
-      const bool gglob = !F32NN && (K > 6 || (p.tab_global && st->gtab_valid));
+      const bool gglob = !F32NN && (K > 6 || ((p.tab_global || p.gtab_tail) && st->gtab_valid));
       const NV* gtab;
       const int* gok;
       if constexpr (F32NN) {
@@ -542,23 +567,11 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
           sm.ybufA[slot][jj][g.a] = AR::yval(active ? (INC && mode == MODE_SWEEP ? yn - yref : yn) : 0.0);
         }
         if (t == ntiles - 1) {
-          // H over the column slots (fixed butterfly order), into Hacc
+          // the per-lane H accumulators to shared memory (the KKT terms are
+          // there already), before the last release: the compute warps
+          // reduce both in the epilogue, off this warp's FP64 chain
 #pragma unroll
-          for (int c = 0; c < K; ++c) {
-#pragma unroll
-            for (int o = LaneGroup<K>::KP; o < 32; o <<= 1) hacc[c] += __shfl_xor_sync(0xffffffffu, hacc[c], o);
-          }
-          if (lane < LaneGroup<K>::KP && ca) {
-#pragma unroll
-            for (int c = 0; c < K; ++c) sm.Hacc[g.a * K + c] = hacc[c];
-          }
-          // the warp's terms (fixed lane order) into slot 0, before the last
-          // release: the compute warps read them in the epilogue
-#pragma unroll
-          for (int e = 0; e < NYT; ++e) {
-            const double v = (e == YT_YMAX) ? warp_max(acc_t[e]) : warp_sum(acc_t[e]);
-            if (lane == 0) sm.yt[0][e] = v;
-          }
+          for (int c = 0; c < K; ++c) sm.lh[lane][c] = hacc[c];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.yready[slot]);
@@ -1204,20 +1217,25 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   }
   __syncthreads();
   // subset table of the new G for the next M pass in global memory: always
-  // for k = 7, 8; for k <= 6 when tab_global (otherwise the M pass builds it)
-  const bool gbuilt = TABLE && (K > 6 || p.tab_global);
-  if constexpr (TABLE) {
-    if (gbuilt) {
-      NnlsSolver<K> gs;
-      gs.init(Gs, 2.220446049250313e-16);
-      build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 0, T, [] { __syncthreads(); });
+  // for k = 7, 8; for k <= 6 with tab_global or gtab_tail (otherwise the M
+  // pass builds it).  Warps 1..15 build it while warp 0 forms the statistics.
+  const bool gbuilt = TABLE && (K > 6 || p.tab_global || p.gtab_tail);
+  double rec[NSTAT];
+  if (warp == 0) {
+    if (mode != MODE_PRIME)
+      // statistics of iterate t: Y half from this sweep's M pass, X half from
+      // the sweep that produced X_t
+      combine_stats_warp(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
+  } else {
+    if constexpr (TABLE) {
+      if (gbuilt) {
+        NnlsSolver<K> gs;
+        gs.init(Gs, 2.220446049250313e-16);
+        build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 32, T - 32, [] { named_sync(3, T - 32); });
+      }
     }
   }
-  double rec[NSTAT];
-  if (warp == 0 && mode != MODE_PRIME)
-    // statistics of iterate t: Y half from this sweep's M pass, X half from
-    // the sweep that produced X_t
-    combine_stats_warp(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
+  __syncthreads();
   if (tid == 0) {
     st->gtab_valid = gbuilt ? 1 : 0;
     double xt[NXT];

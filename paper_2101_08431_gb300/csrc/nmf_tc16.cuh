@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(NT, 1) ypass_tc16_kernel(Problem p, int mode, 
     const int half = lane >> 4, a = lane & 15, wi = warp == W_NN2 ? 1 : 0;
     const int gid = 2 * wi + half;
     LaneNnls16<float> nn;
-    nn.init(sm.Gpf, (float)ArF32::EPS);
+    // the FP32 solve's own tolerance constant, 2^-23 (a finer one would
+    // follow the rounding of this FP32 arithmetic and of B)
+    nn.init(sm.Gpf, 1.1920928955078125e-07f);
     double acc_t[NYT];
 #pragma unroll
     for (int e = 0; e < NYT; ++e) acc_t[e] = 0.0;

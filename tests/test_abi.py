@@ -134,3 +134,10 @@ def test_persistence_arguments_rejected_before_any_device_work(lib, tmp_path):
         p.write_bytes(content)
         assert lib.nmf_load(str(p).encode(), None, C.byref(h)) == _native.NMF_EINVAL
         assert not h.value
+
+
+def test_stage2_arguments_rejected_before_any_device_work(lib):
+    from paper_2101_08431_gb300 import _native
+    z = C.c_void_p(0x1000)
+    assert lib.nmf_ipm(None, 1e-6, 10, None) == _native.NMF_EINVAL
+    assert lib.nmf_ipm_direction(None, z, z, 0.1, 1e-6, 0, z, z, z, z, 0) == _native.NMF_EINVAL
