@@ -540,7 +540,7 @@ def rank16_leg(args, sptr, barrier):
     y_ms = tm["ypass_ms"] / max(tm["ypass_launches"], 1)
     x_ms = tm["xpass_ms"] / max(tm["xpass_launches"], 1)
     alg = n * m * 4 + 2 * m * k * 8 + n * k * 8
-    mma_flops = n * m * 384.0      # issued: B-MMA 64x32x16 per 16 rows x 16 columns, P-MMA 4 x 128x16x16
+    mma_flops = n * m * 256.0      # issued: per element of M, 2 x 128x32x16 MMAs per 128x16 block in each GEMM
     peak, peak_kind = peaks()
     kk = h.objective_kkt()
     h.close()

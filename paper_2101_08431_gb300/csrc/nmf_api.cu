@@ -31,13 +31,15 @@ template <typename TS, typename TM>
 __global__ void append_kernel(const TS* __restrict__ src, long long ld_src, int ncols, TM* M, int ld,
                               int n, int mcap, int first_phys, double* colsq, const double* seed,
                               const uint32_t* seed_mask, DevState* st, double* Y0, double* Y1,
-                              uint32_t* ym0, uint32_t* ym1, int k, unsigned* nonfinite) {
+                              uint32_t* ym0, uint32_t* ym1, int k, unsigned* nonfinite, int mirror) {
   const int c = blockIdx.x;
   if (c >= ncols) return;
   int phys = first_phys + c;
   if (phys >= mcap) phys -= mcap;
   const TS* s = src + (size_t)c * ld_src;
   TM* d = M + (size_t)phys * ld;
+  // the first `mirror` columns of the ring are repeated after its last one
+  TM* d2 = phys < mirror ? M + (size_t)(mcap + phys) * ld : nullptr;
   double acc = 0.0;
   unsigned bad = 0;
   for (int i = threadIdx.x; i < ld; i += blockDim.x) {
@@ -47,6 +49,7 @@ __global__ void append_kernel(const TS* __restrict__ src, long long ld_src, int 
       if (!isfinite((double)v)) ++bad;
     }
     d[i] = v;
+    if (d2) d2[i] = v;
     acc = fma((double)v, (double)v, acc);
   }
   __shared__ double red[32];
@@ -264,8 +267,11 @@ struct nmf_handle {
   ChunkGraph graphs[NVAR];
   // rank 16, mixed precision: the FP32-class pass runs on the tensor cores
   bool tc16 = false;
-  Tc16Plan tc16_L{};              // plan of the last launch, for tc16_m resident columns
+  int mirror = 0;                 // columns mirrored after the ring (tensor-core pass)
+  tc16s::Plan tc16_L{};           // plan of the last launch, for tc16_m resident columns
   int tc16_m = -1;
+  tc16s::Bufs tcb{};              // buffers of the tensor-core pass
+  tc16s::Maps tcmaps{};           // its tensor maps of M
   bool refine_ok = true;          // the FP64-class M passes have a plan for n
   // per-kernel timing (event triplets around each sweep's two launches)
   bool timing = false;
@@ -405,20 +411,26 @@ nmf_status drain_timing(nmf_handle* h) {
   return NMF_OK;
 }
 
+// Plan of the rank-16 tensor-core pass for the current window (kept until
+// the number of resident columns changes); *Q: the partials of P it writes.
+nmf_status tc_plan(nmf_handle* h, int* Q) {
+  if (h->tc16_m != h->m) {
+    if (!tc16s::plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
+      return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
+    h->tc16_m = h->m;
+  }
+  *Q = h->tc16_L.SP;
+  return NMF_OK;
+}
+
 // One sweep (M pass + row pass) or, with mode PRIME, the priming pair;
 // record: this (compensated) sweep records the incremental references.
 nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
   YPlan L{};
-  Tc16Plan T{};
   const bool use_tc = h->tc16 && var == VAR_F32;
   if (use_tc) {
-    if (h->tc16_m != h->m) {
-      if (!tc16_plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
-        return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
-      h->tc16_m = h->m;
-    }
-    T = h->tc16_L;
-    L.Q = T.Q;
+    nmf_status ts = tc_plan(h, &L.Q);
+    if (ts != NMF_OK) return ts;
   } else if (!make_plan(h, var, &L)) {
     return fail(h, NMF_EINVAL, "no launch plan for this shape");
   }
@@ -435,7 +447,8 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
     h->ev_var[h->nev] = var;
     CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][0], h->stream));
   }
-  if (use_tc) CUDA_TRY(h, tc16_launch(p, mode, T, h->stream));
+  int nl = 1;
+  if (use_tc) CUDA_TRY(h, tc16s::launch(p, mode, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
   else CUDA_TRY(h, h->ks[var].ypass(p, mode, L, h->stream));
   if (timed) CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][1], h->stream));
   CUDA_TRY(h, h->ks[var].xpass(p, mode, L.Q, h->nxblk, h->stream));
@@ -443,7 +456,7 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
     CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][2], h->stream));
     h->nev++;
   }
-  h->launches += 2;
+  h->launches += nl + 1;
   return NMF_OK;
 }
 
@@ -613,7 +626,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
                    h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dHg, h->dHtab, h->dHok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1],
-                   h->dShard, h->dShardP};
+                   h->dShard, h->dShardP, h->tcb.Bpart, h->tcb.Xs, h->tcb.Ys, h->tcb.red, h->tcb.ticket};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->hSt) cudaFreeHost(h->hSt);
@@ -663,8 +676,8 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
     // every variant this handle may run must have a plan for n; at rank 16
     // with FP32 M the FP32-class pass is the tensor-core pass, and a handle
     // whose n is beyond the FP64-class kernels runs that pass alone
-    Tc16Plan T{};
-    h->tc16 = h->store_f32 && k == 16 && tc16_plan(h->ld, h->mcap, h->nsm, h->smem_optin, &T);
+    tc16s::Plan T{};
+    h->tc16 = h->store_f32 && k == 16 && tc16s::plan(h->ld, h->mcap, h->nsm, h->smem_optin, &T);
     const int need[3] = {h->store_f32 ? VAR_F32 : VAR_F64, h->store_f32 ? VAR_REF : VAR_F64,
                          h->store_f32 ? VAR_DF : VAR_F64};
     for (int v : need) {
@@ -698,7 +711,8 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   const size_t nk = (size_t)h->n * k, mk = (size_t)h->mcap * k;
   const int Qmax = h->nsm;
   bool ok = true;
-  ok &= cudaMalloc(&h->dM, (size_t)h->ld * h->mcap * (h->store_f32 ? 4 : 8)) == cudaSuccess;
+  h->mirror = h->tc16 ? tc16s::MIRROR : 0;
+  ok &= cudaMalloc(&h->dM, (size_t)h->ld * (h->mcap + h->mirror) * (h->store_f32 ? 4 : 8)) == cudaSuccess;
   for (int b = 0; b < 2; ++b) {
     ok &= dalloc(&h->dX[b], nk) == cudaSuccess;
     ok &= dalloc(&h->dX32[b], nk) == cudaSuccess;
@@ -728,6 +742,13 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   ok &= dalloc(&h->dHpart, (size_t)Qmax * k * k) == cudaSuccess;
   ok &= dalloc(&h->dYterms, (size_t)Qmax * NYT) == cudaSuccess;
   ok &= dalloc(&h->dXpart, (size_t)h->nxblk * (k * k + NXT)) == cudaSuccess;
+  if (h->tc16) {
+    ok &= cudaMalloc(&h->tcb.Bpart, tc16s::bpart_bytes(h->mcap)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.Xs, tc16s::xs_bytes(h->ld)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.Ys, tc16s::ys_bytes(h->mcap)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.red, tc16s::red_bytes(h->nsm)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.ticket, sizeof(unsigned)) == cudaSuccess;
+  }
   ok &= dalloc(&h->dSt, 1) == cudaSuccess;
   ok &= dalloc(&h->dKkt, NSTAT) == cudaSuccess;
   ok &= dalloc(&h->dSeed, KMAX) == cudaSuccess;
@@ -737,8 +758,12 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   ok &= cudaMallocHost(&h->hKkt, sizeof(double) * NSTAT) == cudaSuccess;
   ok &= cudaMallocHost(&h->hNonfinite, sizeof(unsigned)) == cudaSuccess;
   if (!ok) return bail(NMF_ENOMEM, "device allocation failed");
-  cudaMemsetAsync(h->dM, 0, (size_t)h->ld * h->mcap * (h->store_f32 ? 4 : 8), h->stream);
+  cudaMemsetAsync(h->dM, 0, (size_t)h->ld * (h->mcap + h->mirror) * (h->store_f32 ? 4 : 8), h->stream);
   cudaMemsetAsync(h->dSt, 0, sizeof(DevState), h->stream);
+  if (h->tc16) {
+    cudaMemsetAsync(h->tcb.ticket, 0, sizeof(unsigned), h->stream);
+    if (!tc16s::encode_maps(h->dM, h->ld, h->mcap, &h->tcmaps)) return bail(NMF_ECUDA, "tensor maps of M rejected");
+  }
   cudaMemsetAsync(h->dColsq, 0, sizeof(double) * h->mcap, h->stream);
   for (int b = 0; b < 2; ++b) {
     cudaMemsetAsync(h->dY[b], 0, sizeof(double) * mk, h->stream);
@@ -779,23 +804,23 @@ nmf_status nmf_append_columns(nmf_handle* h, const void* cols, int64_t ncols, in
         append_kernel<float, float><<<nc, 256, 0, h->stream>>>(
             (const float*)s, lds, nc, (float*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
             have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
-            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite, h->mirror);
       else
         append_kernel<double, float><<<nc, 256, 0, h->stream>>>(
             (const double*)s, lds, nc, (float*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
             have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
-            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite, h->mirror);
     } else {
       if (dtype == NMF_DTYPE_F32)
         append_kernel<float, double><<<nc, 256, 0, h->stream>>>(
             (const float*)s, lds, nc, (double*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
             have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
-            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite, h->mirror);
       else
         append_kernel<double, double><<<nc, 256, 0, h->stream>>>(
             (const double*)s, lds, nc, (double*)h->dM, h->ld, h->n, h->mcap, fp, h->dColsq,
             have_seed ? h->dSeed : nullptr, have_seed ? h->dSeedMask : nullptr, h->dSt, h->dY[0],
-            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite);
+            h->dY[1], h->dYm[0], h->dYm[1], h->k, h->dNonfinite, h->mirror);
     }
     h->launches++;
     return cudaGetLastError();
@@ -942,23 +967,18 @@ nmf_status nmf_shard_y_half(nmf_handle* h, double* sum_buf, double* max_buf, int
     CUDA_TRY(h, cudaMalloc(&h->dShardP, sizeof(double) * ((size_t)h->ld * h->k + h->k * h->k + NYT)));
   }
   YPlan L{};
-  Tc16Plan T{};
   const bool use_tc = h->tc16 && var == VAR_F32;
   if (use_tc) {
-    if (h->tc16_m != h->m) {
-      if (!tc16_plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
-        return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
-      h->tc16_m = h->m;
-    }
-    T = h->tc16_L;
-    L.Q = T.Q;
+    nmf_status ts = tc_plan(h, &L.Q);
+    if (ts != NMF_OK) return ts;
   } else if (!make_plan(h, var, &L)) {
     return fail(h, NMF_EINVAL, "no launch plan for this shape");
   }
   Problem p = make_problem(h, var);
   p.tab_global = 0;     // H is formed from the reduced buffers by the X half
   CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
-  if (use_tc) CUDA_TRY(h, tc16_launch(p, MODE_SWEEP, T, h->stream));
+  int nl = 1;
+  if (use_tc) CUDA_TRY(h, tc16s::launch(p, MODE_SWEEP, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
   else CUDA_TRY(h, h->ks[var].ypass(p, MODE_SWEEP, L, h->stream));
   double* out = h->dShard;
   double* outmax = h->dShard + len;
@@ -966,7 +986,7 @@ nmf_status nmf_shard_y_half(nmf_handle* h, double* sum_buf, double* max_buf, int
   if (var == VAR_F32) shard_export_kernel<float><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
   else if (var == VAR_DF) shard_export_kernel<DF><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
   else shard_export_kernel<double><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
-  h->launches += 2;
+  h->launches += nl + 1;
   CUDA_TRY(h, cudaGetLastError());
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CUDA_TRY(h, cudaMemcpyAsync(sum_buf, out, sizeof(double) * len, kind, h->stream));
@@ -1107,25 +1127,20 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
   // rows) the tensor-core pass
   const int var = h->store_f32 ? (h->refine_ok ? VAR_REF : VAR_F32) : VAR_F64;
   YPlan L{};
-  Tc16Plan T{};
   const bool use_tc = h->tc16 && var == VAR_F32;
   if (use_tc) {
-    if (h->tc16_m != h->m) {
-      if (!tc16_plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
-        return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
-      h->tc16_m = h->m;
-    }
-    T = h->tc16_L;
-    L.Q = T.Q;
+    nmf_status ts = tc_plan(h, &L.Q);
+    if (ts != NMF_OK) return ts;
   } else if (!make_plan(h, var, &L)) {
     return fail(h, NMF_EINVAL, "no launch plan for this shape");
   }
   Problem p = make_problem(h, var);
   CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
-  if (use_tc) CUDA_TRY(h, tc16_launch(p, MODE_KKT, T, h->stream));
+  int nl = 1;
+  if (use_tc) CUDA_TRY(h, tc16s::launch(p, MODE_KKT, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
   else CUDA_TRY(h, h->ks[var].ypass(p, MODE_KKT, L, h->stream));
   kkt_stats_kernel<<<1, 32, 0, h->stream>>>(p, L.Q, h->dKkt);
-  h->launches += 2;
+  h->launches += nl + 1;
   CUDA_TRY(h, cudaGetLastError());
   CUDA_TRY(h, cudaMemcpyAsync(h->hKkt, h->dKkt, sizeof(double) * NSTAT, cudaMemcpyDeviceToHost, h->stream));
   nmf_status s = read_state(h);
@@ -1316,6 +1331,10 @@ nmf_status nmf_load(const char* path, void* cuda_stream, nmf_handle** out) {
   // the window lands in physical columns 0 .. m-1 (head 0); every partition
   // of the sweep follows logical column order, so results do not depend on it
   bool ok = cudaMemcpyAsync(h->dM, pm, (size_t)hd.ld * m * esz, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (h->mirror > 0 && m > 0)   // the mirrored columns after the ring
+    ok = ok && cudaMemcpyAsync(static_cast<char*>(h->dM) + (size_t)hd.ld * h->mcap * esz, h->dM,
+                               (size_t)hd.ld * std::min<size_t>(m, (size_t)h->mirror) * esz,
+                               cudaMemcpyDeviceToDevice, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(h->dColsq, pcol, m * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(h->dY[cur], py, m * k * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(h->dYm[cur], pym, m * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;

@@ -844,7 +844,8 @@ struct XSmem {
   // value type of the row solves: FP64 in every pass (see YTraits::F32NN)
   static constexpr bool F32NN = false;
   using SV = typename std::conditional<F32NN, float, double>::type;
-  // k = 16: value type of the 16-lane row solves
+  // k = 16: value type of the 16-lane row solves of the FP64-class passes;
+  // the tensor-core (FP32-class) pass solves its rows in FP32 (HpF)
   using V16 = double;
   // Lawson-Hanson tolerance constant of the FP64 row solves: 2^-52, but 2^-23
   // at rank 16 with FP32 partials (the tensor-core pass: its P carries ~1e-5,
@@ -861,6 +862,7 @@ struct XSmem {
     double yfin[NYT];
     double gram_w[NWN][K * K];
     V16 Hp[K][K + 1];                  // k = 16: H, padded rows, in the solves' type
+    float HpF[K][K + 1];               // k = 16: H in FP32 (the tensor-core pass's row solves)
     double term_w[NWN][16];
     unsigned ticket;
   };
@@ -1109,13 +1111,20 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     using V16 = typename Xs::V16;
     auto& gram_w = xs.gram_w;
     auto& term_w = xs.term_w;
-    for (int e = tid; e < K * K; e += T) xs.Hp[e / K][e % K] = (V16)H[e];
+    for (int e = tid; e < K * K; e += T) {
+      xs.Hp[e / K][e % K] = (V16)H[e];
+      xs.HpF[e / K][e % K] = (float)H[e];
+    }
     __syncthreads();
     const int half = lane >> 4, a = lane & 15;
     const int lrow = warp * 2 + half, grow_i = row0 + lrow;
     const bool ract = grow_i < p.n;   // uniform on the 16 lanes of a row
-    LaneNnls16<V16> nn;
-    nn.init(xs.Hp, (V16)(p.inc ? 5.684341886080802e-14 : Xs::EPS));
+    const int gbase = lane & 16;
+    const unsigned ggm = 0xFFFFu << gbase;
+    // FP32 partials outside the incremental sweeps come from the tensor-core
+    // pass (P good to ~1e-5): its rows are solved in FP32 like its columns,
+    // with the FP32 tolerance constant 2^-23; every other pass solves in FP64
+    const bool f32solve = std::is_same<TA, float>::value && !p.inc;
     double pr = 0.0, xo = 0.0;
     uint32_t old_mask = 0;
     if (ract) {
@@ -1130,12 +1139,20 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     uint32_t msk = 0;
     int stt = 0;
     if (ract) {
-      if (mode == MODE_SWEEP) {
+      if (mode == MODE_SWEEP && f32solve) {
+        LaneNnls16<float> nf;
+        nf.init(xs.HpF, 1.1920928955078125e-07f);
+        float xv = (float)xo;
+        stt = nf.solve((float)pr, xv, p.warm != 0, &msk);
+        xn = (double)xv;
+      } else if (mode == MODE_SWEEP) {
+        LaneNnls16<V16> nn;
+        nn.init(xs.Hp, (V16)(p.inc ? 5.684341886080802e-14 : Xs::EPS));
         V16 xv = (V16)xo;
         stt = nn.solve((V16)pr, xv, p.warm != 0, &msk);
         xn = (double)xv;
       } else {
-        msk = (__ballot_sync(nn.gm, dpos(xo)) >> nn.base) & 0xFFFFu;
+        msk = (__ballot_sync(ggm, dpos(xo)) >> gbase) & 0xFFFFu;
       }
     }
     // X-half KKT terms of the iterate leaving this sweep: graX = H x - P;
@@ -1144,7 +1161,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     double gr[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      const double xc = __shfl_sync(nn.gm, xn, nn.base + c);
+      const double xc = __shfl_sync(ggm, xn, gbase + c);
       gx = fmad(H[a * K + c], xc, gx);
       gr[c] = ract ? xn * xc : 0.0;
     }

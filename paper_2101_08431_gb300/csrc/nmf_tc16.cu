@@ -1,6 +1,10 @@
-// Host side of the rank-16 tensor-core M pass: launch plan and launch.
+// Host side of the rank-16 tensor-core M passes: launch plans and launches.
+#include <algorithm>
+
+#include <cudaTypedefs.h>
+
 #include "nmf.h"
-#include "nmf_tc16.cuh"
+#include "nmf_tc16s.cuh"
 
 namespace nmfgb {
 
@@ -101,6 +105,117 @@ cudaError_t tc16_launch(const Problem& p, int mode, const Tc16Plan& L, cudaStrea
   cfg.stream = s;
   return cudaLaunchKernelEx(&cfg, tc16::ypass_tc16_kernel, p, mode, L);
 }
+
+namespace tc16s {
+
+size_t bpart_bytes(int mcap) { return (size_t)8 * (size_t)mcap * K * sizeof(float); }
+size_t xs_bytes(int ld) { return (size_t)ld * 64; }
+size_t ys_bytes(int mcap) { return (size_t)((mcap + PG_COLS - 1) / PG_COLS) * PG_COLS * 64; }
+size_t red_bytes(int nsm) { return (size_t)3 * (size_t)std::max(1, nsm) * RED * sizeof(double); }
+
+namespace {
+
+// splits s in 1..smax minimising the time of `units1 * s` equal units on
+// `slots` CTAs relative to one unit per CTA (waves / s), plus a small charge
+// per split for the partials it writes
+int best_splits(int units1, int smax, int slots) {
+  int best = 1;
+  double bc = 1e30;
+  for (int s = 1; s <= std::max(1, smax); ++s) {
+    const long long u = (long long)units1 * s;
+    const double c = (double)((u + slots - 1) / slots) / s + 0.01 * s;
+    if (c < bc - 1e-12) {
+      bc = c;
+      best = s;
+    }
+  }
+  return best;
+}
+
+void set_attr() {
+  static bool done[64] = {false};
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  bool ok = cudaFuncSetAttribute(bgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(pgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess;
+  if (ok) done[dev] = true;
+  else cudaGetLastError();
+}
+
+}  // namespace
+
+bool encode_maps(void* M, int ld, int mcap, Maps* out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)mcap + MIRROR};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t es[2] = {1, 1};
+  const cuuint32_t boxb[2] = {SLAB_ROWS, BG_COLS}, boxp[2] = {SLAB_ROWS, PG_COLS};
+  bool ok = encode(&out->b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, M, dims, strides, boxb, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  ok = ok && encode(&out->p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, M, dims, strides, boxp, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return ok;
+}
+
+bool plan(int ld, int m, int nsm, int smem_optin, Plan* out) {
+  if (ld < 32 || ld % 32 != 0 || m < 1 || nsm < 1) return false;
+  Plan L{};
+  L.NSB = std::min(NSMAX, (smem_optin - CTL_BYTES) / BG_STAGE);
+  L.NSP = std::min(NSMAX, (smem_optin - CTL_BYTES) / PG_STAGE);
+  if (L.NSB < 2 || L.NSP < 2) return false;
+  L.smemB = (size_t)CTL_BYTES + (size_t)L.NSB * BG_STAGE;
+  L.smemP = (size_t)CTL_BYTES + (size_t)L.NSP * PG_STAGE;
+  const int ngran = ld / 32;
+  const int ntile = (m + BG_COLS - 1) / BG_COLS;
+  // every row split keeps at least 64 rows (two 32-row granules)
+  L.SB = best_splits(ntile, std::min(8, std::max(1, ngran / 2)), nsm);
+  L.gridB = std::min(ntile * L.SB, nsm);
+  const int nrb = (ld + PG_ROWS - 1) / PG_ROWS;
+  const int ncg = (m + PG_COLS - 1) / PG_COLS;
+  L.SP = best_splits(nrb, std::min(16, ncg), nsm);
+  L.gridP = std::min(nrb * L.SP, nsm);
+  const int ncolp = ncg * PG_COLS;
+  L.gridS = std::min((ncolp + SOLVE_T / 16 - 1) / (SOLVE_T / 16), 3 * nsm);   // three blocks per SM
+  *out = L;
+  return true;
+}
+
+cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, const Maps& T, cudaStream_t s,
+                   int* nl) {
+  set_attr();
+  int n = 0;
+  if (mode != MODE_PRIME) {
+    const int tot = p.ld * K;
+    xsplit_kernel<<<std::min((tot + 255) / 256, 1024), 256, 0, s>>>(p, B);
+    bgemm_kernel<<<L.gridB, NT, L.smemB, s>>>(T.b, p, B, L);
+    n += 2;
+  }
+  solve_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, L, mode);
+  ++n;
+  if (mode != MODE_KKT) {
+    pgemm_kernel<<<L.gridP, NT, L.smemP, s>>>(T.p, p, B, L);
+    ++n;
+  }
+  if (nl) *nl = n;
+  return cudaGetLastError();
+}
+
+}  // namespace tc16s
 
 namespace {
 

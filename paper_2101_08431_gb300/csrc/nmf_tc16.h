@@ -3,6 +3,7 @@
 
 #include <cstddef>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "nmf_common.cuh"
@@ -27,5 +28,53 @@ struct Tc16Plan {
 bool tc16_shape(int ld, int C, int smem_optin, Tc16Plan* out);
 bool tc16_plan(int ld, int m, int nsm, int smem_optin, Tc16Plan* out);
 cudaError_t tc16_launch(const Problem& p, int mode, const Tc16Plan& L, cudaStream_t s);
+
+// The rank-16 pass in three streaming launches (nmf_tc16s.cuh).
+namespace tc16s {
+
+// Columns of the ring mirrored after its last column (M holds mcap + MIRROR
+// columns; column mcap + j repeats column j for j < MIRROR), so that a tile
+// of up to MIRROR consecutive window columns is one box of the tensor map.
+constexpr int MIRROR = 128;
+
+// Buffers of the pass (device memory of the handle).
+struct Bufs {
+  float* Bpart;               // [SB][mcap][16]: B partials, window column order
+  unsigned char* Xs;          // split of X: ld/8 blocks of 512 bytes
+  unsigned char* Ys;          // split of Y: one block of 512 bytes per 8 window columns
+  double* red;                // [gridS][16 * 16 + NYT] block partials of the solve kernel
+  unsigned* ticket;           // last-block ticket of the solve kernel (self-resetting)
+};
+
+struct Plan {
+  int SB, SP;                 // row splits of the B-GEMM, column splits of the P-GEMM
+  int gridB, gridP, gridS;
+  int NSB, NSP;               // stages of the two TMA rings
+  size_t smemB, smemP;
+};
+
+// Tensor maps of M (FP32, ld rows x mcap + MIRROR columns, 128-byte swizzle)
+// with the boxes of the two GEMMs: 32 rows x 128 columns and 32 x 64.
+struct Maps {
+  CUtensorMap b, p;
+};
+
+// Sizes of the buffers for ld rows and mcap columns on nsm SMs (bytes).
+size_t bpart_bytes(int mcap);
+size_t xs_bytes(int ld);
+size_t ys_bytes(int mcap);
+size_t red_bytes(int nsm);
+// false when the driver entry point is missing or rejects the shape
+bool encode_maps(void* M, int ld, int mcap, Maps* out);
+// Plan for ld rows and m resident columns (host arithmetic only); false if
+// the shared memory of a CTA cannot hold two stages of either ring.
+bool plan(int ld, int m, int nsm, int smem_optin, Plan* out);
+// The launches of one M pass: MODE_SWEEP / MODE_KKT: X split, B-GEMM, solves
+// (+ P-GEMM for SWEEP); MODE_PRIME: solves (masks, H) and P-GEMM.  Returns
+// the number of launches in *nl.
+cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, const Maps& T, cudaStream_t s,
+                   int* nl);
+
+}  // namespace tc16s
 
 }  // namespace nmfgb
