@@ -272,6 +272,11 @@ struct nmf_handle {
   int tc16_m = -1;
   tc16s::Bufs tcb{};              // buffers of the tensor-core pass
   tc16s::Maps tcmaps{};           // its tensor maps of M
+  // rank 16 beyond the rows of the cluster-fused FP64-class kernels: the
+  // refinement runs the compensated reference and incremental passes
+  bool tc_refine = false;
+  RefPlan tcR{};
+  double* dBdf = nullptr;         // B partials of the reference pass
   bool refine_ok = true;          // the FP64-class M passes have a plan for n
   // per-kernel timing (event triplets around each sweep's two launches)
   bool timing = false;
@@ -415,7 +420,8 @@ nmf_status drain_timing(nmf_handle* h) {
 // the number of resident columns changes); *Q: the partials of P it writes.
 nmf_status tc_plan(nmf_handle* h, int* Q) {
   if (h->tc16_m != h->m) {
-    if (!tc16s::plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L))
+    if (!tc16s::plan(h->ld, h->m, h->nsm, h->smem_optin, &h->tc16_L) ||
+        (h->tc_refine && !tc16r::plan(h->ld, h->m, h->nsm, &h->tcR)))
       return fail(h, NMF_EINVAL, "no tensor-core launch plan for this shape");
     h->tc16_m = h->m;
   }
@@ -427,7 +433,7 @@ nmf_status tc_plan(nmf_handle* h, int* Q) {
 // record: this (compensated) sweep records the incremental references.
 nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
   YPlan L{};
-  const bool use_tc = h->tc16 && var == VAR_F32;
+  const bool use_tc = h->tc16 && (var == VAR_F32 || h->tc_refine);
   if (use_tc) {
     nmf_status ts = tc_plan(h, &L.Q);
     if (ts != NMF_OK) return ts;
@@ -436,6 +442,9 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
   }
   Problem p = make_problem(h, var);
   p.record_refs = record ? 1 : 0;
+  // the row pass of the rank-16 refinement passes: FP64 partials (reference
+  // sweeps) or FP32 partials of the change (incremental sweeps)
+  const int xvar = (use_tc && var != VAR_F32) ? (var == VAR_INC ? VAR_F32 : VAR_REF) : var;
   const bool timed = h->timing && mode == MODE_SWEEP;
   if (timed && h->nev == nmf_handle::NEV) {
     nmf_status s = drain_timing(h);
@@ -448,10 +457,15 @@ nmf_status launch_pair(nmf_handle* h, int var, int mode, bool record = false) {
     CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][0], h->stream));
   }
   int nl = 1;
-  if (use_tc) CUDA_TRY(h, tc16s::launch(p, mode, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
-  else CUDA_TRY(h, h->ks[var].ypass(p, mode, L, h->stream));
+  if (use_tc && var == VAR_F32)
+    CUDA_TRY(h, tc16s::launch(p, mode, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
+  else if (use_tc)
+    CUDA_TRY(h, tc16r::launch(p, mode, var == VAR_INC ? tc16r::INC_PASS : tc16r::REF_PASS, h->tcR, h->tc16_L, h->tcb,
+                              h->tcmaps, h->dBdf, h->stream, &nl, &L.Q));
+  else
+    CUDA_TRY(h, h->ks[var].ypass(p, mode, L, h->stream));
   if (timed) CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][1], h->stream));
-  CUDA_TRY(h, h->ks[var].xpass(p, mode, L.Q, h->nxblk, h->stream));
+  CUDA_TRY(h, h->ks[xvar].xpass(p, mode, L.Q, h->nxblk, h->stream));
   if (timed) {
     CUDA_TRY(h, cudaEventRecord(h->ev[h->nev][2], h->stream));
     h->nev++;
@@ -626,7 +640,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
                    h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dHg, h->dHtab, h->dHok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1],
-                   h->dShard, h->dShardP, h->tcb.Bpart, h->tcb.Xs, h->tcb.Ys, h->tcb.red, h->tcb.ticket};
+                   h->dShard, h->dShardP, h->tcb.Bpart, h->tcb.Xs, h->tcb.Ys, h->tcb.red, h->tcb.ticket, h->dBdf};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->hSt) cudaFreeHost(h->hSt);
@@ -693,7 +707,11 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
       }
       if (!ok) return bail(NMF_EINVAL, "n too large for the kernels of this precision");
     }
-    if (h->store_f32 && h->refine_ok && h->has[VAR_INC]) {
+    if (h->tc16 && !h->refine_ok) {   // the rank-16 reference and incremental passes refine
+      h->tc_refine = true;
+      h->refine_ok = true;
+      h->inc_ok = true;
+    } else if (h->store_f32 && h->refine_ok && h->has[VAR_INC]) {
       YPlan L;
       int msave = h->m;
       h->m = h->mcap;
@@ -748,6 +766,7 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
     ok &= cudaMalloc(&h->tcb.Ys, tc16s::ys_bytes(h->mcap)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.red, tc16s::red_bytes(h->nsm)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.ticket, sizeof(unsigned)) == cudaSuccess;
+    if (h->tc_refine) ok &= cudaMalloc(&h->dBdf, tc16r::bdf_bytes(h->ld, h->mcap)) == cudaSuccess;
   }
   ok &= dalloc(&h->dSt, 1) == cudaSuccess;
   ok &= dalloc(&h->dKkt, NSTAT) == cudaSuccess;
@@ -967,7 +986,7 @@ nmf_status nmf_shard_y_half(nmf_handle* h, double* sum_buf, double* max_buf, int
     CUDA_TRY(h, cudaMalloc(&h->dShardP, sizeof(double) * ((size_t)h->ld * h->k + h->k * h->k + NYT)));
   }
   YPlan L{};
-  const bool use_tc = h->tc16 && var == VAR_F32;
+  const bool use_tc = h->tc16 && (var == VAR_F32 || h->tc_refine);
   if (use_tc) {
     nmf_status ts = tc_plan(h, &L.Q);
     if (ts != NMF_OK) return ts;
@@ -978,13 +997,18 @@ nmf_status nmf_shard_y_half(nmf_handle* h, double* sum_buf, double* max_buf, int
   p.tab_global = 0;     // H is formed from the reduced buffers by the X half
   CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
   int nl = 1;
-  if (use_tc) CUDA_TRY(h, tc16s::launch(p, MODE_SWEEP, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
-  else CUDA_TRY(h, h->ks[var].ypass(p, MODE_SWEEP, L, h->stream));
+  if (use_tc && var == VAR_F32)
+    CUDA_TRY(h, tc16s::launch(p, MODE_SWEEP, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
+  else if (use_tc)
+    CUDA_TRY(h, tc16r::launch(p, MODE_SWEEP, tc16r::REF_PASS, h->tcR, h->tc16_L, h->tcb, h->tcmaps, h->dBdf,
+                              h->stream, &nl, &L.Q));
+  else
+    CUDA_TRY(h, h->ks[var].ypass(p, MODE_SWEEP, L, h->stream));
   double* out = h->dShard;
   double* outmax = h->dShard + len;
   const int nb = std::max(1, std::min(h->nsm, (int)(((size_t)h->n * h->k + 255) / 256)));
   if (var == VAR_F32) shard_export_kernel<float><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
-  else if (var == VAR_DF) shard_export_kernel<DF><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
+  else if (var == VAR_DF && !use_tc) shard_export_kernel<DF><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
   else shard_export_kernel<double><<<nb, 256, 0, h->stream>>>(p, L.Q, out, outmax);
   h->launches += nl + 1;
   CUDA_TRY(h, cudaGetLastError());
@@ -1127,7 +1151,7 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
   // rows) the tensor-core pass
   const int var = h->store_f32 ? (h->refine_ok ? VAR_REF : VAR_F32) : VAR_F64;
   YPlan L{};
-  const bool use_tc = h->tc16 && var == VAR_F32;
+  const bool use_tc = h->tc16 && (var == VAR_F32 || h->tc_refine);
   if (use_tc) {
     nmf_status ts = tc_plan(h, &L.Q);
     if (ts != NMF_OK) return ts;
@@ -1137,8 +1161,13 @@ nmf_status nmf_objective_kkt(nmf_handle* h, double* f, double* kkt_abs, double* 
   Problem p = make_problem(h, var);
   CUDA_TRY(h, cudaMemsetAsync(&h->dSt->done, 0, sizeof(int), h->stream));
   int nl = 1;
-  if (use_tc) CUDA_TRY(h, tc16s::launch(p, MODE_KKT, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
-  else CUDA_TRY(h, h->ks[var].ypass(p, MODE_KKT, L, h->stream));
+  if (use_tc && var == VAR_F32)
+    CUDA_TRY(h, tc16s::launch(p, MODE_KKT, h->tc16_L, h->tcb, h->tcmaps, h->stream, &nl));
+  else if (use_tc)
+    CUDA_TRY(h, tc16r::launch(p, MODE_KKT, tc16r::REF_PASS, h->tcR, h->tc16_L, h->tcb, h->tcmaps, h->dBdf,
+                              h->stream, &nl, &L.Q));
+  else
+    CUDA_TRY(h, h->ks[var].ypass(p, MODE_KKT, L, h->stream));
   kkt_stats_kernel<<<1, 32, 0, h->stream>>>(p, L.Q, h->dKkt);
   h->launches += nl + 1;
   CUDA_TRY(h, cudaGetLastError());

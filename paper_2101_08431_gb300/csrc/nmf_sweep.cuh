@@ -844,8 +844,9 @@ struct XSmem {
   // value type of the row solves: FP64 in every pass (see YTraits::F32NN)
   static constexpr bool F32NN = false;
   using SV = typename std::conditional<F32NN, float, double>::type;
-  // k = 16: value type of the 16-lane row solves of the FP64-class passes;
-  // the tensor-core (FP32-class) pass solves its rows in FP32 (HpF)
+  // k = 16: value type of the 16-lane row solves (FP64 in every pass: an
+  // FP32 solve with its 2^-23 tolerance leaves out variables worth percents
+  // of a row where H is ill conditioned)
   using V16 = double;
   // Lawson-Hanson tolerance constant of the FP64 row solves: 2^-52, but 2^-23
   // at rank 16 with FP32 partials (the tensor-core pass: its P carries ~1e-5,
@@ -862,7 +863,7 @@ struct XSmem {
     double yfin[NYT];
     double gram_w[NWN][K * K];
     V16 Hp[K][K + 1];                  // k = 16: H, padded rows, in the solves' type
-    float HpF[K][K + 1];               // k = 16: H in FP32 (the tensor-core pass's row solves)
+    float HpF[K][K + 1];               // k = 16: H in FP32 (the tensor-core pass's predictor solves)
     double term_w[NWN][16];
     unsigned ticket;
   };
@@ -1121,39 +1122,77 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     const bool ract = grow_i < p.n;   // uniform on the 16 lanes of a row
     const int gbase = lane & 16;
     const unsigned ggm = 0xFFFFu << gbase;
-    // FP32 partials outside the incremental sweeps come from the tensor-core
-    // pass (P good to ~1e-5): its rows are solved in FP32 like its columns,
-    // with the FP32 tolerance constant 2^-23; every other pass solves in FP64
-    const bool f32solve = std::is_same<TA, float>::value && !p.inc;
+    // the row's right-hand side P_i (+ P_ref in incremental sweeps)
+    auto prow = [&](int r) -> double {
+      TA ts = psum[0][r][a];
+      for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][r][a]);
+      double v = PartOps<TA>::to_double(ts);
+      if (p.inc && mode == MODE_SWEEP) v += p.Pref[(size_t)(row0 + r) * K + a];
+      return v;
+    };
     double pr = 0.0, xo = 0.0;
     uint32_t old_mask = 0;
     if (ract) {
-      TA ts = psum[0][lrow][a];
-      for (int w = 1; w < npw; ++w) ts = PartOps<TA>::add(ts, psum[w][lrow][a]);
-      pr = PartOps<TA>::to_double(ts);
-      if (p.inc && mode == MODE_SWEEP) pr += p.Pref[(size_t)grow_i * K + a];
+      pr = prow(lrow);
       xo = p.X[cur][(size_t)grow_i * K + a];
       old_mask = p.xmask[cur][grow_i];
     }
     double xn = xo;
     uint32_t msk = 0;
     int stt = 0;
-    if (ract) {
-      if (mode == MODE_SWEEP && f32solve) {
+    if (ract && mode == MODE_SWEEP) {
+      bool done = false;
+      bool warm = p.warm != 0;
+      if (std::is_same<TA, float>::value && !p.inc) {
+        // the tensor-core pass: an FP32 solve finds the passive set P (its
+        // FP64 row solves cost a cold inverse of H_PP per row at ~1/60 of the
+        // FP32 rate), two steps of iterative refinement on P with the FP64
+        // residual give x to FP64-level accuracy, and an FP64 optimality
+        // test (x_P > 0, no gradient above the entering tolerance outside P)
+        // accepts it; otherwise the FP64 solve continues from there
         LaneNnls16<float> nf;
         nf.init(xs.HpF, 1.1920928955078125e-07f);
         float xv = (float)xo;
-        stt = nf.solve((float)pr, xv, p.warm != 0, &msk);
+        stt = nf.solve((float)pr, xv, warm, &msk);
         xn = (double)xv;
-      } else if (mode == MODE_SWEEP) {
+        if (stt == 0 && msk == nf.Pc) {
+          const bool inP = (msk >> a) & 1u;
+#pragma unroll 1
+          for (int it = 0; it < 2; ++it) {
+            double rr = pr;
+#pragma unroll
+            for (int c = 0; c < K; ++c) rr = fmad(-H[a * K + c], __shfl_sync(ggm, xn, gbase + c), rr);
+            const float dz = nf.apply(msk, (float)rr);
+            if (inP) xn += (double)dz;
+          }
+          double w = pr, hmax = 0.0;
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            w = fmad(-H[a * K + c], __shfl_sync(ggm, xn, gbase + c), w);
+            hmax = dmax_nn(hmax, dabs(H[c * K + c]));
+          }
+          double bmax = dabs(pr), xmax = inP ? dabs(xn) : 0.0;
+#pragma unroll
+          for (int o = 8; o >= 1; o >>= 1) {
+            bmax = dmax_nn(bmax, __shfl_xor_sync(ggm, bmax, o));
+            xmax = dmax_nn(xmax, __shfl_xor_sync(ggm, xmax, o));
+          }
+          const double tol = 10.0 * K * Xs::EPS * (bmax + hmax * xmax);
+          const bool bad = inP ? !(xn > 0.0) : (w > tol);
+          done = ((__ballot_sync(ggm, bad) >> gbase) & 0xFFFFu) == 0;
+          if (!inP) xn = 0.0;
+          warm = true;   // a fallback starts from the refined x
+        }
+      }
+      if (!done) {
         LaneNnls16<V16> nn;
         nn.init(xs.Hp, (V16)(p.inc ? 5.684341886080802e-14 : Xs::EPS));
-        V16 xv = (V16)xo;
-        stt = nn.solve((V16)pr, xv, p.warm != 0, &msk);
+        V16 xv = (V16)xn;
+        stt = nn.solve((V16)pr, xv, warm, &msk);
         xn = (double)xv;
-      } else {
-        msk = (__ballot_sync(ggm, dpos(xo)) >> gbase) & 0xFFFFu;
       }
+    } else if (ract) {
+      msk = (__ballot_sync(ggm, dpos(xo)) >> gbase) & 0xFFFFu;
     }
     // X-half KKT terms of the iterate leaving this sweep: graX = H x - P;
     // Gram partial: row a of x x^T

@@ -4,7 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include "nmf.h"
-#include "nmf_tc16s.cuh"
+#include "nmf_tc16r.cuh"
 
 namespace nmfgb {
 
@@ -132,6 +132,8 @@ int best_splits(int units1, int smax, int slots) {
   return best;
 }
 
+}  // namespace
+
 void set_attr() {
   static bool done[64] = {false};
   int dev = 0, optin = 0;
@@ -143,8 +145,6 @@ void set_attr() {
   if (ok) done[dev] = true;
   else cudaGetLastError();
 }
-
-}  // namespace
 
 bool encode_maps(void* M, int ld, int mcap, Maps* out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -189,8 +189,15 @@ bool plan(int ld, int m, int nsm, int smem_optin, Plan* out) {
   const int ncg = (m + PG_COLS - 1) / PG_COLS;
   L.SP = best_splits(nrb, std::min(16, ncg), nsm);
   L.gridP = std::min(nrb * L.SP, nsm);
+  // column solves: a group's columns run in sequence, each from the inverse
+  // of G_PP carried from its left neighbour (neighbouring columns share most
+  // of their passive set), so a group takes several columns: about one
+  // 16-group block per SM, at most 16 columns per group
   const int ncolp = ncg * PG_COLS;
-  L.gridS = std::min((ncolp + SOLVE_T / 16 - 1) / (SOLVE_T / 16), 3 * nsm);   // three blocks per SM
+  L.cpg = std::max(1, std::min(16, (ncolp + nsm * (SOLVE_T / 16) - 1) / (nsm * (SOLVE_T / 16))));
+  const int ngroups = (ncolp + L.cpg - 1) / L.cpg;
+  L.gridS = (ngroups + SOLVE_T / 16 - 1) / (SOLVE_T / 16);
+  if (L.gridS > 3 * nsm) return false;
   *out = L;
   return true;
 }
@@ -216,6 +223,69 @@ cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, con
 }
 
 }  // namespace tc16s
+
+namespace tc16r {
+
+size_t bdf_bytes(int ld, int mcap) { return (size_t)((ld + BR - 1) / BR) * (size_t)mcap * K * sizeof(double); }
+
+bool plan(int ld, int m, int nsm, RefPlan* out) {
+  if (ld < 32 || ld % 32 != 0 || m < 1 || nsm < 1) return false;
+  RefPlan R{};
+  // two CTAs per SM for both kernels
+  R.nrbB = (ld + BR - 1) / BR;
+  R.slicesB = std::max(1, std::min(m, (2 * nsm + R.nrbB - 1) / R.nrbB));
+  R.gridB = R.nrbB * R.slicesB;
+  R.nrbP = (ld + TP - 1) / TP;
+  R.SPd = std::max(1, std::min(std::min(m, nsm), (2 * nsm) / R.nrbP));
+  R.gridP = R.nrbP * R.SPd;
+  *out = R;
+  return true;
+}
+
+namespace {
+void set_attr_ref() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  if (cudaFuncSetAttribute(dfb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dfb_smem()) == cudaSuccess)
+    done[dev] = true;
+  else
+    cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch(const Problem& p, int mode, int pass, const RefPlan& R, const tc16s::Plan& L,
+                   const tc16s::Bufs& B, const tc16s::Maps& T, double* Bdf, cudaStream_t s, int* nl, int* Q) {
+  set_attr_ref();
+  tc16s::set_attr();
+  int n = 0;
+  if (pass == REF_PASS) {
+    *Q = R.SPd;
+    if (mode != MODE_PRIME) {
+      dfb_kernel<<<R.gridB, TB, dfb_smem(), s>>>(p, Bdf, R);
+      ++n;
+    }
+    solve64_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, Bdf, R, L.cpg, R.nrbB, R.SPd, REF, mode);
+    ++n;
+    if (mode != MODE_KKT) {
+      dfp_kernel<<<R.gridP, TP, 0, s>>>(p, R, mode);
+      ++n;
+    }
+  } else {
+    *Q = L.SP;
+    const int tot = p.ld * K;
+    xdsplit_kernel<<<std::min((tot + 255) / 256, 1024), 256, 0, s>>>(p, B);
+    tc16s::bgemm_kernel<<<L.gridB, tc16s::NT, L.smemB, s>>>(T.b, p, B, L);
+    solve64_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, Bdf, R, L.cpg, L.SB, L.SP, INC, mode);
+    tc16s::pgemm_kernel<<<L.gridP, tc16s::NT, L.smemP, s>>>(T.p, p, B, L);
+    n += 4;
+  }
+  if (nl) *nl = n;
+  return cudaGetLastError();
+}
+
+}  // namespace tc16r
 
 namespace {
 

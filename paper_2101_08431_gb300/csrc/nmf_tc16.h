@@ -49,6 +49,7 @@ struct Bufs {
 struct Plan {
   int SB, SP;                 // row splits of the B-GEMM, column splits of the P-GEMM
   int gridB, gridP, gridS;
+  int cpg;                    // consecutive columns per 16-lane group of the solve kernel
   int NSB, NSP;               // stages of the two TMA rings
   size_t smemB, smemP;
 };
@@ -76,5 +77,26 @@ cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, con
                    int* nl);
 
 }  // namespace tc16s
+
+// Reference (compensated) and incremental sweeps of the rank-16 refinement
+// where n is beyond the cluster-fused FP64-class kernels (nmf_tc16r.cuh).
+struct RefPlan {
+  int nrbB, slicesB, gridB;   // B partials: row blocks x column slices
+  int nrbP, SPd, gridP;       // P partials: 256-row blocks x column splits (= Q of the row pass)
+};
+
+namespace tc16r {
+
+enum Pass { REF_PASS = 0, INC_PASS = 1 };
+size_t bdf_bytes(int ld, int mcap);
+bool plan(int ld, int m, int nsm, RefPlan* out);
+// The M pass of a reference sweep (pass REF_PASS: compensated B and P, FP64
+// solves; MODE_KKT: B and the terms only; MODE_PRIME: masks, H and P) or of
+// an incremental sweep (INC_PASS: tensor-core change terms, FP64 solves).
+// *Q: the P partials the row pass sums; *nl: launches.
+cudaError_t launch(const Problem& p, int mode, int pass, const RefPlan& R, const tc16s::Plan& L,
+                   const tc16s::Bufs& B, const tc16s::Maps& T, double* Bdf, cudaStream_t s, int* nl, int* Q);
+
+}  // namespace tc16r
 
 }  // namespace nmfgb

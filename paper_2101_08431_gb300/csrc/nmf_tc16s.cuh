@@ -615,9 +615,8 @@ __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, P
   nn.init(Gf, 1.1920928955078125e-07f);
   const int a = nn.a;
   const int ncols = p.m, ncolp = (ncols + PG_COLS - 1) / PG_COLS * PG_COLS;
-  const int ngroups = gridDim.x * (SOLVE_T / 16), gid = blockIdx.x * (SOLVE_T / 16) + (tid >> 4);
-  const int cpg = (ncolp + ngroups - 1) / ngroups;
-  const int cbeg = min(ncolp, gid * cpg), cend = min(ncolp, cbeg + cpg);
+  const int gid = blockIdx.x * (SOLVE_T / 16) + (tid >> 4);
+  const int cbeg = min(ncolp, gid * L.cpg), cend = min(ncolp, cbeg + L.cpg);
   float acc_t[NYT];
 #pragma unroll
   for (int e = 0; e < NYT; ++e) acc_t[e] = 0.f;

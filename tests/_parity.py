@@ -98,8 +98,9 @@ PASS_UNITS = {
     # FP32 products and sums; FP64 solves
     "f32": dict(u=lambda L: 2.0 ** -24 + 2.0 * (L - 1) * 2.0 ** -24, kappa=2.0 ** -40, eps=2.0 ** -52),
     # split-BF16 products (2^-15, tests/test_split_bf16_bound.py), FP32 sums;
-    # FP32 column and row solves
-    "tc16": dict(u=lambda L: 2.0 ** -15 + 2.0 * (L - 1) * 2.0 ** -24, kappa=2.0 ** -18, eps=2.0 ** -23),
+    # FP32 column solves (kappa, eps), FP64 row solves (kappa_x, eps_x)
+    "tc16": dict(u=lambda L: 2.0 ** -15 + 2.0 * (L - 1) * 2.0 ** -24, kappa=2.0 ** -18, kappa_x=2.0 ** -40,
+                 eps=2.0 ** -23, eps_x=2.0 ** -23),
 }
 
 

@@ -1,5 +1,5 @@
 """GPU parity of the rank-16 tensor-core M pass (split-BF16 tcgen05
-contractions, FP32 column and row solves), through the C ABI.
+contractions, FP32 column solves, FP64 row solves), through the C ABI.
 
 The FP32-class pass of the mixed form at k = 16 runs B = X^T M and P = M Y^T
 as (M_hi + M_lo)(V_hi + V_lo) BF16 products with FP32 accumulation.  Each of
@@ -255,3 +255,83 @@ def test_tc16_bounded_wait_reports_timeout():
     assert 0.15 < dt < 30.0, dt
     x = torch.ones(16, device="cuda")
     assert float(x.sum().item()) == 16.0        # the device still answers
+
+
+# ---------------------------------------------------------------------------
+# Refinement at rank 16 beyond the rows of the cluster-fused FP64-class kernels
+# (n > ~3840): compensated reference sweeps and incremental sweeps
+# ---------------------------------------------------------------------------
+REF_N, REF_M, REF_SEED = 4100, 290, 8
+
+
+def _refined_state(sweeps):
+    """A state of the refinement phase: oracle sweeps from near the generating
+    factors (FP64 throughout)."""
+    return _warm_state(REF_N, REF_M, REF_SEED, sweeps=sweeps)
+
+
+def test_tc16_reference_sweep_matches_the_oracle():
+    """Pass mode 2 at n = 4100, k = 16: the compensated reference sweep
+    (double-float B = X^T M and P = M Y^T, FP64 column and row solves)
+    against one oracle sweep: per column / row within 1e-7 (the compensated
+    pass's bar) and the subproblem objective within its first-order bound
+    with the compensated contraction unit."""
+    S = _lib()
+    M32, M64, X, Y = _refined_state(40)
+    h = S(REF_N, 16, REF_M, prec=1, kkt_target=0.0)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    h.set_pass_mode(2)
+    h.sweep(1)
+    Xg, Yg, xmg, ymg = h.get_factors()
+    h.close()
+    Xo, Yo, _, _, _ = oracle.sweep(M64, X, Y)
+    ey, ex = colmax_rel(Yg, Yo, axis=0), colmax_rel(Xg, Xo, axis=1)
+    ry, rx, _ = objective_ratios(M64, X, Xg, Yg, "df")
+    print("reference sweep n=%d m=%d: per-column %.2e per-row %.2e; objective ratios %.2e %.2e" %
+          (REF_N, REF_M, ey, ex, ry, rx))
+    assert ey <= 1e-7 and ex <= 1e-7
+    assert ry <= 1.0 and rx <= 1.0
+
+
+def test_tc16_incremental_chunk_matches_the_oracle():
+    """Pass mode 3 at n = 4100, k = 16: a chunk of one recording reference
+    sweep and 31 incremental sweeps (tensor-core change terms on the FP64
+    references) against 32 oracle sweeps from the same refined state: per
+    column / row within 1e-7."""
+    S = _lib()
+    M32, M64, X, Y = _refined_state(40)
+    h = S(REF_N, 16, REF_M, prec=1, kkt_target=0.0)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    h.set_pass_mode(3)
+    h.sweep(32)
+    Xg, Yg, _, _ = h.get_factors()
+    h.close()
+    Xo, Yo, _, _, _, _, _ = oracle.anls(M64, X, Y, max_sweeps=32)
+    ey, ex = colmax_rel(Yg, Yo, axis=0), colmax_rel(Xg, Xo, axis=1)
+    print("32 sweeps (1 reference + 31 incremental): per-column %.2e per-row %.2e" % (ey, ex))
+    assert ey <= 1e-7 and ex <= 1e-7
+
+
+def test_tc16_mixed_run_reaches_the_target_the_oracle_certifies():
+    """The mixed schedule at n = 4100, k = 16 (tensor-core passes, then the
+    reference / incremental refinement) to relative KKT 1e-8 from a state
+    near the generating factors: the oracle's KKT of the returned iterate is
+    within the target.  (The run's own f is measured through the change
+    terms' 2^-15 rounding, which the cancellation in the Gram form of f
+    amplifies; it is checked loosely.)"""
+    S = _lib()
+    M32, M64, X, Y = _refined_state(0)
+    h = S(REF_N, 16, REF_M, prec=1, kkt_target=1e-8, max_sweeps=40000)
+    h.append_columns(M32)
+    h.set_factors(X, Y)
+    st = h.sweep(0)
+    Xg, Yg, _, _ = h.get_factors()
+    h.close()
+    kk = oracle.kkt(M64, Xg, Yg)
+    print("mixed run: %d sweeps (%d refinement), f %.12e (oracle %.12e), rel KKT %.3e (oracle %.3e)" %
+          (st["sweeps"], st["fp64_sweeps"], st["f"], kk["f"], st["kkt_rel"], kk["rel"]))
+    assert st["converged"] == 1 and st["fp64_sweeps"] > 0
+    assert kk["rel"] <= 1.05e-8
+    assert st["f"] == pytest.approx(kk["f"], rel=1e-3)

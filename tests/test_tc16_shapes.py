@@ -67,6 +67,8 @@ int main() {
           CHECK(L.SP >= 1 && L.SP <= nsm, "SP %d", L.SP);   // P, H, terms partials: nsm slabs allocated
           CHECK(L.gridB >= 1 && L.gridB <= nsm && L.gridP >= 1 && L.gridP <= nsm, "grids");
           CHECK((size_t)L.gridS * RED * 8 <= red_bytes(nsm), "red");
+          CHECK(L.cpg >= 1 && (long long)L.gridS * (SOLVE_T / 16) * L.cpg >= (long long)((m + PG_COLS - 1) / PG_COLS) * PG_COLS,
+                "solve groups cover the padded window");
           // ---- B-GEMM
           const int ntile = (m + BG_COLS - 1) / BG_COLS;
           const int nunits = ntile * L.SB;
