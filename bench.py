@@ -498,6 +498,7 @@ def mask_differences(ym, xm, ref):
 
 
 K16_N, K16_M, K16_K, K16_NOISE, K16_PRECOND = 8192, 16384, 16, 1e-4, 30
+K16_CAP = 100000
 
 
 def rank16_leg(args, sptr, barrier):
@@ -544,8 +545,11 @@ def rank16_leg(args, sptr, barrier):
     peak, peak_kind = peaks()
     kk = h.objective_kkt()
     h.close()
+    ttk = None if args.skip_k16_ttk else rank16_to_target(M32, X0, Y0, sptr, barrier)
     return {"workload": "PDF-like n=8192 m=16384 k=16 (1e-4 rel. noise), FP32 M (512 MB), tensor-core "
-                        "FP32-class pass (split-BF16 tcgen05 contractions, FP32 solves, FP64 Grams and KKT terms)",
+                        "FP32-class pass (split-BF16 tcgen05 contractions: B-GEMM and P-GEMM launches with the "
+                        "column solves between them; FP32 column solves, FP64-checked row solves)",
+            "time_to_kkt": ttk,
             "state": "timed sweeps follow %d sweeps from the U[0,1] start" % K16_PRECOND,
             "l2": "inputs larger than L2 (no flush)",
             "sweeps_per_s": steps / (ms / 1e3), "ms_per_sweep": ms / steps,
@@ -555,6 +559,35 @@ def rank16_leg(args, sptr, barrier):
             "ypass_mma_tflops_issued": mma_flops / (y_ms / 1e3) / 1e12,
             "columns_per_s": m * steps / (ms / 1e3),
             "kkt_rel_after": kk["kkt_rel"], "f_after": kk["f"]}
+
+
+def rank16_to_target(M32, X0, Y0, sptr, barrier):
+    """The mixed form at n=8192, m=16384, k=16 from the U[0,1] start to
+    relative KKT 1e-8: tensor-core passes, then chunks of a compensated
+    reference sweep and incremental sweeps; one run timed with CUDA events on
+    the library's stream, the returned iterate certified by the oracle's KKT
+    (FP64, the whole matrix)."""
+    import torch
+    import oracle
+    from paper_2101_08431_gb300 import NMF_PREC_MIXED, StreamingNMF
+    n, m, k = K16_N, K16_M, K16_K
+    stream = torch.cuda.current_stream()
+    h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=1e-8, max_sweeps=K16_CAP, stream=sptr)
+    h.append_columns(M32)
+    h.set_factors(X0, Y0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    st = h.sweep(0, allow_notconv=True)
+    e1.record(stream)
+    barrier()
+    secs = e0.elapsed_time(e1) / 1e3
+    Xg, Yg, _, _ = h.get_factors()
+    h.close()
+    kk = oracle.kkt(M32.astype(np.float64), Xg, Yg)
+    return {"seconds": secs, "sweeps": st["sweeps"], "refinement_sweeps": st["fp64_sweeps"],
+            "converged": bool(st["converged"]), "kkt_rel": st["kkt_rel"], "sweep_cap": K16_CAP,
+            "oracle": {"kkt_rel": kk["rel"], "f": kk["f"], "note": "oracle_kkt of the returned iterate, FP64"}}
 
 
 # The paper's synthetic experiments (Sec. 5.4: X, Y ~ U[0,1], M = XY + N(0, 0.1^2),
@@ -930,6 +963,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-problem batched leg")
     ap.add_argument("--skip-serve", action="store_true", help="skip the streaming-serving leg")
     ap.add_argument("--skip-k16", action="store_true", help="skip the rank-16 tensor-core leg")
+    ap.add_argument("--skip-k16-ttk", action="store_true",
+                    help="skip the rank-16 run to relative KKT 1e-8 (inside the rank-16 leg)")
     ap.add_argument("--skip-batch-ttk", action="store_true",
                     help="skip the batched-vs-FP64 time to relative KKT 1e-8 on a subset of the batch")
     ap.add_argument("--skip-paper", action="store_true", help="skip the paper-shape runs to E <= 1e-6")

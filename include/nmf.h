@@ -127,11 +127,17 @@ void nmf_config_init(nmf_config *cfg);
  * a warp per problem) and k = 16 (one 16-lane group per problem, the
  * tensor-core contractions of the mixed form); other ranks are rejected.
  * Rank 16 with NMF_PREC_MIXED: the FP32-class pass runs on the tensor cores
- * (split-BF16 contractions, FP32 solves; about 1e-5 relative in B and P).
- * Where n is beyond the rows of the FP64-class kernels at rank 16 (n above
- * about 3840), the handle runs that pass alone: the automatic schedule never
- * leaves it, pass modes 1 and 2 run it as well, and nmf_objective_kkt
- * measures with it. */
+ * (split-BF16 contractions, about 1e-5 relative in B and P, in two streaming
+ * launches with the FP32 column solves between them; row solves predicted in
+ * FP32, refined and checked in FP64).
+ * Where n is beyond the rows of the cluster-fused FP64-class kernels at rank
+ * 16 (n above about 3840), the refinement runs the rank-16 reference pass
+ * (compensated FP32 "double-float" B = X^T M and P = M Y^T, FP64 solves;
+ * pass modes 1 and 2, the recording sweep of mode 3, the priming pass and
+ * nmf_objective_kkt) and the incremental pass (tensor-core contractions of
+ * the change of X and Y since the reference sweep added to its FP64
+ * contractions; mode 3).  Such a handle also holds M with its first 128
+ * columns repeated after the ring (tensor copies never wrap). */
 nmf_status nmf_create(const nmf_config *cfg, nmf_handle **out);
 
 /* The configuration the handle was created with (its cuda_stream field is
