@@ -924,7 +924,7 @@ def run_ncu_case(args):
         b.close()
         print("ncu case batch: 16 problems, 3 sweeps")
         return 0
-    if args.ncu_case == "k16":
+    if args.ncu_case in ("k16", "k16inc"):
         import synth
         n, m, k = K16_N, 6144, K16_K     # 192 MB of FP32 M: above L2, a small device footprint
         M, _, _ = synth.pdf_like(n, m, k, noise=K16_NOISE, relative=True, seed=11)
@@ -932,11 +932,13 @@ def run_ncu_case(args):
         h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=0.0)
         h.append_columns(np.asfortranarray(M, dtype=np.float32))
         h.set_factors(X, Y)
-        h.set_pass_mode(0)
+        # k16: tensor-core FP32-class sweeps; k16inc: chunks of a compensated
+        # reference sweep and incremental sweeps
+        h.set_pass_mode(0 if args.ncu_case == "k16" else 3)
         h.sweep(args.ncu_precond + 3, want_stats=False)
         torch.cuda.synchronize()
         h.close()
-        print("ncu case k16: n=%d m=%d, 1 priming pair + %d sweeps" % (n, m, args.ncu_precond + 3))
+        print("ncu case %s: n=%d m=%d, 1 priming pair + %d sweeps" % (args.ncu_case, n, m, args.ncu_precond + 3))
         return 0
     M32, M64, X0, Y0 = make_data(0)
     fp64 = args.ncu_case == "f64"
@@ -971,7 +973,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--batch-ttk", action="store_true",
                     help="also run every batched problem to relative KKT 1e-8")
-    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "inc", "batch", "k16"], default=None,
+    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "inc", "batch", "k16", "k16inc"], default=None,
                     help="run only a short launch sequence for an ncu capture")
     ap.add_argument("--ncu-precond", type=int, default=200)
     args = ap.parse_args()

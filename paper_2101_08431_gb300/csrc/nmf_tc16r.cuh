@@ -73,9 +73,14 @@ __global__ void __launch_bounds__(TB, 2) dfb_kernel(Problem p, double* Bdf, RefP
     DF acc[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) acc[c] = ArDF::zero();
-    for (int t = 0; t < nt; ++t) {
+    float mv[BR / 32];   // the column's rows of the block, all loads in flight at once
+#pragma unroll
+    for (int t = 0; t < BR / 32; ++t) mv[t] = t < nt ? __ldg(mc + lane + 32 * t) : 0.f;
+#pragma unroll
+    for (int t = 0; t < BR / 32; ++t) {
+      if (t >= nt) break;
       const int i = lane + 32 * t;
-      const float m = __ldg(mc + i);
+      const float m = mv[t];
       const float4* h4 = reinterpret_cast<const float4*>(xh + i * XSTR);
       const float4* l4 = reinterpret_cast<const float4*>(xl + i * XSTR);
 #pragma unroll
@@ -121,8 +126,16 @@ __global__ void __launch_bounds__(TP) dfp_kernel(Problem p, RefPlan R, int mode)
     }
     __syncthreads();
     if (row < p.ld) {
+      constexpr int PF = 8;   // columns whose M values are loaded ahead
+      float mv[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u)
+        mv[u] = u < nc ? __ldg(M + (size_t)wrap_col(p.head, j0 + u, p.mcap) * p.ld + row) : 0.f;
       for (int jj = 0; jj < nc; ++jj) {
-        const float m = __ldg(M + (size_t)wrap_col(p.head, j0 + jj, p.mcap) * p.ld + row);
+        const float m = mv[0];
+#pragma unroll
+        for (int u = 0; u < PF - 1; ++u) mv[u] = mv[u + 1];
+        mv[PF - 1] = jj + PF < nc ? __ldg(M + (size_t)wrap_col(p.head, j0 + jj + PF, p.mcap) * p.ld + row) : 0.f;
         const float4* h4 = reinterpret_cast<const float4*>(&yh[jj][0]);
         const float4* l4 = reinterpret_cast<const float4*>(&yl[jj][0]);
 #pragma unroll
