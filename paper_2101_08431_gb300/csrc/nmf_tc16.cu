@@ -77,20 +77,24 @@ bool encode_maps(void* M, int ld, int mcap, Maps* out) {
 bool plan(int ld, int m, int nsm, int smem_optin, Plan* out) {
   if (ld < 32 || ld % 32 != 0 || m < 1 || nsm < 1) return false;
   Plan L{};
-  L.NSB = std::min(NSMAX, (smem_optin - CTL_BYTES) / BG_STAGE);
-  L.NSP = std::min(NSMAX, (smem_optin - CTL_BYTES) / PG_STAGE);
+  // two CTAs per SM: each holds at most half of the SM's shared memory (the
+  // opt-in limit plus the 1 KB the SM reserves per CTA)
+  const int half = (smem_optin + 1024) / 2 - 1024;
+  const int slots = 2 * nsm;
+  L.NSB = std::min(NSMAX, (half - CTL_BYTES) / BG_STAGE);
+  L.NSP = std::min(NSMAX, (half - CTL_BYTES) / PG_STAGE);
   if (L.NSB < 2 || L.NSP < 2) return false;
   L.smemB = (size_t)CTL_BYTES + (size_t)L.NSB * BG_STAGE;
   L.smemP = (size_t)CTL_BYTES + (size_t)L.NSP * PG_STAGE;
   const int ngran = ld / 32;
   const int ntile = (m + BG_COLS - 1) / BG_COLS;
   // every row split keeps at least 64 rows (two 32-row granules)
-  L.SB = best_splits(ntile, std::min(8, std::max(1, ngran / 2)), nsm);
-  L.gridB = std::min(ntile * L.SB, nsm);
+  L.SB = best_splits(ntile, std::min(8, std::max(1, ngran / 2)), slots);
+  L.gridB = std::min(ntile * L.SB, slots);
   const int nrb = (ld + PG_ROWS - 1) / PG_ROWS;
   const int ncg = (m + PG_COLS - 1) / PG_COLS;
-  L.SP = best_splits(nrb, std::min(16, ncg), nsm);
-  L.gridP = std::min(nrb * L.SP, nsm);
+  L.SP = best_splits(nrb, std::min(16, ncg), slots);
+  L.gridP = std::min(nrb * L.SP, slots);
   // column solves: a group's columns run in sequence, each from the inverse
   // of G_PP carried from its left neighbour (neighbouring columns share most
   // of their passive set), so a group takes several columns: about one

@@ -47,8 +47,11 @@ using tc16::split2;
 using tc16::WAIT_NS;
 
 constexpr int K = 16;
-constexpr int NT = 512;            // threads of the GEMM kernels
-constexpr int W_PROD = 0, W_MMA = 1, W_EPI = 4, W_CV = 8, NCV = 8;
+// GEMM CTAs: warps 0-3 epilogue (TMEM lane quarters 0-3), 4 producer, 5 MMA
+// issue, 6-9 converters; two CTAs per SM (two independent rings)
+constexpr int NT = 320;            // threads of the GEMM kernels
+constexpr int W_EPI = 0, W_PROD = 4, W_MMA = 5, W_CV = 6, NCV = 4;
+constexpr int CV_ITEMS = 1024 / (NCV * 32);   // (column, 8-row group) items per converter thread per chunk
 constexpr int NSMAX = 6;
 constexpr int CTL_BYTES = 1024;
 constexpr int SLAB_ROWS = 32;      // rows of one tensor copy (128 bytes of FP32: the swizzle span)
@@ -81,6 +84,7 @@ struct Ctl {
   int abort_flag;
 };
 static_assert(sizeof(Ctl) <= CTL_BYTES, "control block");
+static_assert(CV_ITEMS == 8, "converter maps: 4 warps x 8 items x 32 lanes = 128 columns x 8 row groups");
 
 // byte offset of (row or column index i, operand column n in 0..31) in the
 // split operands of X (i = row) and Y (i = window column): 8 indices x 32
@@ -195,7 +199,7 @@ __host__ __device__ __forceinline__ void bg_unit(const Problem& p, int SB, int u
   r1 = (int)(((long long)(split + 1) * ngran) / SB) * 32;
 }
 
-__global__ void __launch_bounds__(NT, 1) bgemm_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, Bufs bf,
+__global__ void __launch_bounds__(NT, 2) bgemm_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, Bufs bf,
                                                       Plan L) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Ctl& sm = *reinterpret_cast<Ctl*>(smem_raw);
@@ -333,10 +337,10 @@ __global__ void __launch_bounds__(NT, 1) bgemm_kernel(const __grid_constant__ CU
         const bool ok = warp_wait(sm, &sm.full[s], (uint32_t)((gc / NS) & 1));
         unsigned char* stg = stages + (size_t)s * BG_STAGE;
         const int ng = rows / 8;
-        float4 v[4][2];
+        float4 v[CV_ITEMS][2];
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          const int j = 8 * (w + 8 * (uu & 1)) + jl, g = gq + 4 * (uu >> 1);
+        for (int uu = 0; uu < CV_ITEMS; ++uu) {
+          const int j = 8 * (w + NCV * (uu & 3)) + jl, g = gq + 4 * (uu >> 2);
           v[uu][0] = v[uu][1] = make_float4(0.f, 0.f, 0.f, 0.f);
           if (ok && g < ng) {   // rows 8g .. 8g+7: slab g / 4, chunks 2 (g % 4) and 2 (g % 4) + 1
             const unsigned char* sl = stg + (g >> 2) * BG_SLAB;
@@ -350,8 +354,8 @@ __global__ void __launch_bounds__(NT, 1) bgemm_kernel(const __grid_constant__ CU
           break;
         }
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          const int j = 8 * (w + 8 * (uu & 1)) + jl, g = gq + 4 * (uu >> 1);
+        for (int uu = 0; uu < CV_ITEMS; ++uu) {
+          const int j = 8 * (w + NCV * (uu & 3)) + jl, g = gq + 4 * (uu >> 2);
           if (g < ng) {
             uint4 hi, lo;
             split2(v[uu][0].x, v[uu][0].y, hi.x, lo.x);
@@ -400,7 +404,7 @@ __host__ __device__ __forceinline__ void pg_unit(const Problem& p, int SP, int u
   g1 = (int)(((long long)(split + 1) * ncg) / SP);
 }
 
-__global__ void __launch_bounds__(NT, 1) pgemm_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, Bufs bf,
+__global__ void __launch_bounds__(NT, 2) pgemm_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, Bufs bf,
                                                       Plan L) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Ctl& sm = *reinterpret_cast<Ctl*>(smem_raw);
@@ -535,11 +539,11 @@ __global__ void __launch_bounds__(NT, 1) pgemm_kernel(const __grid_constant__ CU
         const int s = gc % NS;
         const bool ok = warp_wait(sm, &sm.full[s], (uint32_t)((gc / NS) & 1));
         unsigned char* stg = stages + (size_t)s * PG_STAGE;
-        const int j = 8 * w + jl;   // column of the chunk (K index)
-        float4 v[4][2];
+        float4 v[CV_ITEMS][2];
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          const int g8 = gq + 4 * uu;   // 8-row group (M index)
+        for (int uu = 0; uu < CV_ITEMS; ++uu) {
+          const int j = 8 * (w + NCV * (uu & 1)) + jl;   // column of the chunk (K index)
+          const int g8 = gq + 4 * (uu >> 1);              // 8-row group (M index)
           v[uu][0] = v[uu][1] = make_float4(0.f, 0.f, 0.f, 0.f);
           if (ok && j < nv && g8 < ng) {   // rows 8 g8 .. 8 g8 + 7: slab g8 / 4
             const unsigned char* sl = stg + (g8 >> 2) * PG_SLAB;
@@ -553,8 +557,9 @@ __global__ void __launch_bounds__(NT, 1) pgemm_kernel(const __grid_constant__ CU
           break;
         }
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          const int g8 = gq + 4 * uu;
+        for (int uu = 0; uu < CV_ITEMS; ++uu) {
+          const int j = 8 * (w + NCV * (uu & 1)) + jl;
+          const int g8 = gq + 4 * (uu >> 1);
           uint4 hi, lo;   // columns beyond the window and rows beyond ld are written as zero
           split2(v[uu][0].x, v[uu][0].y, hi.x, lo.x);
           split2(v[uu][0].z, v[uu][0].w, hi.y, lo.y);

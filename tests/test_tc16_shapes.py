@@ -65,7 +65,9 @@ int main() {
           CHECK(CTL_BYTES % 1024 == 0 && BG_STAGE % 1024 == 0 && PG_STAGE % 1024 == 0, "slab alignment");
           CHECK(L.SB >= 1 && (size_t)L.SB * mcap * 16 * 4 <= bpart_bytes(mcap), "Bpart ld %d m %d SB %d", ld, m, L.SB);
           CHECK(L.SP >= 1 && L.SP <= nsm, "SP %d", L.SP);   // P, H, terms partials: nsm slabs allocated
-          CHECK(L.gridB >= 1 && L.gridB <= nsm && L.gridP >= 1 && L.gridP <= nsm, "grids");
+          CHECK(L.gridB >= 1 && L.gridB <= 2 * nsm && L.gridP >= 1 && L.gridP <= 2 * nsm, "grids");
+          CHECK(2 * (L.smemB + 1024) <= (size_t)optin + 1024 && 2 * (L.smemP + 1024) <= (size_t)optin + 1024,
+                "two CTAs per SM");
           CHECK((size_t)L.gridS * RED * 8 <= red_bytes(nsm), "red");
           CHECK(L.cpg >= 1 && (long long)L.gridS * (SOLVE_T / 16) * L.cpg >= (long long)((m + PG_COLS - 1) / PG_COLS) * PG_COLS,
                 "solve groups cover the padded window");
