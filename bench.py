@@ -583,11 +583,24 @@ def rank16_to_target(M32, X0, Y0, sptr, barrier):
     barrier()
     secs = e0.elapsed_time(e1) / 1e3
     Xg, Yg, _, _ = h.get_factors()
+    # the refinement's passes near convergence: 64 more sweeps of pass mode 3
+    # (chunks of a reference sweep and incremental sweeps) with per-pass events
+    h.set_pass_mode(3)
+    h.set_timing(True)
+    h.sweep(64, want_stats=False, allow_notconv=True)
+    passes = {}
+    for name in ("df", "inc"):
+        t = h.get_pass_timing(name)
+        if t["sweeps"]:
+            passes[name] = {"sweeps": t["sweeps"], "ypass_avg_ms": t["ypass_ms"] / t["sweeps"],
+                            "xpass_avg_ms": t["xpass_ms"] / t["sweeps"]}
+    h.set_timing(False)
     h.close()
     kk = oracle.kkt(M32.astype(np.float64), Xg, Yg)
     return {"seconds": secs, "sweeps": st["sweeps"], "refinement_sweeps": st["fp64_sweeps"],
             "converged": bool(st["converged"]), "kkt_rel": st["kkt_rel"], "sweep_cap": K16_CAP,
-            "oracle": {"kkt_rel": kk["rel"], "f": kk["f"], "note": "oracle_kkt of the returned iterate, FP64"}}
+            "oracle": {"kkt_rel": kk["rel"], "f": kk["f"], "note": "oracle_kkt of the returned iterate, FP64"},
+            "refinement_passes_near_convergence": passes}
 
 
 # The paper's synthetic experiments (Sec. 5.4: X, Y ~ U[0,1], M = XY + N(0, 0.1^2),

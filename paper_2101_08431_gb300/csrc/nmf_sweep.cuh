@@ -858,7 +858,7 @@ struct XSmem {
     double H[K * K];
     double Gs[K * K];
     SV Hn[K * K];                      // H in the solve's type
-    TA psum[Tr::NW][Tr::RB][K];
+    TA psum[Tr::NW][Tr::RB][K + 1];   // padded: a lane's K values start on another bank
     double fin[Tr::NV];
     double yfin[NYT];
     double gram_w[NWN][K * K];
@@ -1068,7 +1068,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       }
       if (lane < KP && ca) {
 #pragma unroll
-        for (int c = 0; c < K; ++c) gram_w[warp][g.a * K + c] = gr[c];
+        for (int c = 0; c < K; ++c) gram_w[warp][c * K + g.a] = gr[c];   // G is symmetric: conflict-free order
       }
       const double mx = warp_max(tv[XT_XMAX]);
       tv[XT_XMAX] = 0.0;
@@ -1143,46 +1143,22 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     if (ract && mode == MODE_SWEEP) {
       bool done = false;
       bool warm = p.warm != 0;
-      if (std::is_same<TA, float>::value && !p.inc) {
-        // the tensor-core pass: an FP32 solve finds the passive set P (its
-        // FP64 row solves cost a cold inverse of H_PP per row at ~1/60 of the
-        // FP32 rate), two steps of iterative refinement on P with the FP64
-        // residual give x to FP64-level accuracy, and an FP64 optimality
-        // test (x_P > 0, no gradient above the entering tolerance outside P)
-        // accepts it; otherwise the FP64 solve continues from there
+      if (std::is_same<TA, float>::value) {
+        // FP32 partials: the tensor-core pass and the incremental sweeps.  An
+        // FP32 solve predicts the passive set (an FP64 solve pays a cold
+        // inverse of H_PP per row at ~1/60 of the FP32 rate), FP64-residual
+        // refinement gives x, and an FP64 optimality test accepts it;
+        // otherwise the FP64 solve continues from the refined x
         LaneNnls16<float> nf;
         nf.init(xs.HpF, 1.1920928955078125e-07f);
-        float xv = (float)xo;
-        stt = nf.solve((float)pr, xv, warm, &msk);
-        xn = (double)xv;
-        if (stt == 0 && msk == nf.Pc) {
-          const bool inP = (msk >> a) & 1u;
-#pragma unroll 1
-          for (int it = 0; it < 2; ++it) {
-            double rr = pr;
+        double hmax = 0.0;
 #pragma unroll
-            for (int c = 0; c < K; ++c) rr = fmad(-H[a * K + c], __shfl_sync(ggm, xn, gbase + c), rr);
-            const float dz = nf.apply(msk, (float)rr);
-            if (inP) xn += (double)dz;
-          }
-          double w = pr, hmax = 0.0;
-#pragma unroll
-          for (int c = 0; c < K; ++c) {
-            w = fmad(-H[a * K + c], __shfl_sync(ggm, xn, gbase + c), w);
-            hmax = dmax_nn(hmax, dabs(H[c * K + c]));
-          }
-          double bmax = dabs(pr), xmax = inP ? dabs(xn) : 0.0;
-#pragma unroll
-          for (int o = 8; o >= 1; o >>= 1) {
-            bmax = dmax_nn(bmax, __shfl_xor_sync(ggm, bmax, o));
-            xmax = dmax_nn(xmax, __shfl_xor_sync(ggm, xmax, o));
-          }
-          const double tol = 10.0 * K * Xs::EPS * (bmax + hmax * xmax);
-          const bool bad = inP ? !(xn > 0.0) : (w > tol);
-          done = ((__ballot_sync(ggm, bad) >> gbase) & 0xFFFFu) == 0;
-          if (!inP) xn = 0.0;
-          warm = true;   // a fallback starts from the refined x
-        }
+        for (int c = 0; c < K; ++c) hmax = dmax_nn(hmax, dabs(H[c * K + c]));
+        done = p.inc ? predict_refine16(nf, H + a * K, hmax, pr, xn, &msk, &stt, warm, 5.684341886080802e-14,
+                                        1.4210854715202004e-14, 8)
+                     : predict_refine16(nf, H + a * K, hmax, pr, xn, &msk, &stt, warm, Xs::EPS,
+                                        9.094947017729282e-13, 2);
+        warm = true;   // a fallback starts from the refined x
       }
       if (!done) {
         LaneNnls16<V16> nn;
@@ -1209,7 +1185,7 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     for (int c = 0; c < K; ++c) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], 16);
     if (lane < 16) {
 #pragma unroll
-      for (int c = 0; c < K; ++c) gram_w[warp][a * K + c] = gr[c];
+      for (int c = 0; c < K; ++c) gram_w[warp][c * K + a] = gr[c];   // G is symmetric: conflict-free order
     }
     double tv[16];
 #pragma unroll
