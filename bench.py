@@ -583,11 +583,16 @@ def rank16_to_target(M32, X0, Y0, sptr, barrier):
     barrier()
     secs = e0.elapsed_time(e1) / 1e3
     Xg, Yg, _, _ = h.get_factors()
-    # the refinement's passes near convergence: 64 more sweeps of pass mode 3
-    # (chunks of a reference sweep and incremental sweeps) with per-pass events
+    h.close()
+    # the refinement's passes near convergence: 64 sweeps of pass mode 3
+    # (chunks of a reference sweep and incremental sweeps) from the returned
+    # iterate, with per-pass events, on a handle without a stopping target
+    h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=0.0, stream=sptr)
+    h.append_columns(M32)
+    h.set_factors(Xg, Yg)
     h.set_pass_mode(3)
     h.set_timing(True)
-    h.sweep(64, want_stats=False, allow_notconv=True)
+    h.sweep(64, want_stats=False)
     passes = {}
     for name in ("df", "inc"):
         t = h.get_pass_timing(name)
@@ -937,6 +942,30 @@ def run_ncu_case(args):
         b.close()
         print("ncu case batch: 16 problems, 3 sweeps")
         return 0
+    if args.ncu_case == "k16near":
+        # the refinement's incremental sweeps near convergence: a mixed run to
+        # relative KKT 1e-7, then a fresh handle from that iterate, pass mode 3
+        import synth
+        n, m, k = K16_N, 6144, K16_K
+        M, _, _ = synth.pdf_like(n, m, k, noise=K16_NOISE, relative=True, seed=11)
+        M32 = np.asfortranarray(M, dtype=np.float32)
+        X, Y = synth.init_factors(n, m, k, seed=11)
+        h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=1e-7, max_sweeps=20000)
+        h.append_columns(M32)
+        h.set_factors(X, Y)
+        h.sweep(0, want_stats=False, allow_notconv=True)
+        X, Y, _, _ = h.get_factors()
+        h.close()
+        h = StreamingNMF(n, k, m, prec=NMF_PREC_MIXED, kkt_target=0.0)
+        h.append_columns(M32)
+        h.set_factors(X, Y)
+        h.set_pass_mode(3)
+        h.sweep(args.ncu_precond + 3, want_stats=False)
+        torch.cuda.synchronize()
+        h.close()
+        print("ncu case k16near: n=%d m=%d, a run to rel-KKT 1e-7, then 1 priming pair + %d sweeps of mode 3" %
+              (n, m, args.ncu_precond + 3))
+        return 0
     if args.ncu_case in ("k16", "k16inc"):
         import synth
         n, m, k = K16_N, 6144, K16_K     # 192 MB of FP32 M: above L2, a small device footprint
@@ -986,7 +1015,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--batch-ttk", action="store_true",
                     help="also run every batched problem to relative KKT 1e-8")
-    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "inc", "batch", "k16", "k16inc"], default=None,
+    ap.add_argument("--ncu-case", choices=["f32", "ref", "f64", "df", "inc", "batch", "k16", "k16inc", "k16near"], default=None,
                     help="run only a short launch sequence for an ncu capture")
     ap.add_argument("--ncu-precond", type=int, default=200)
     args = ap.parse_args()

@@ -640,7 +640,8 @@ nmf_status nmf_destroy(nmf_handle* h) {
                    h->dYm[0], h->dYm[1], h->dXm[0], h->dXm[1], h->dG, h->dGtab, h->dGok, h->dHg, h->dHtab, h->dHok, h->dColsq, h->dPpart,
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1],
-                   h->dShard, h->dShardP, h->tcb.Bpart, h->tcb.Xs, h->tcb.Ys, h->tcb.red, h->tcb.ticket, h->dBdf};
+                   h->dShard, h->dShardP, h->tcb.Bpart, h->tcb.Xs, h->tcb.Ys, h->tcb.red, h->tcb.ticket, h->tcb.perm, h->tcb.perm_tmp,
+                   h->tcb.keys, h->dBdf};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->hSt) cudaFreeHost(h->hSt);
@@ -766,6 +767,9 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
     ok &= cudaMalloc(&h->tcb.Ys, tc16s::ys_bytes(h->mcap)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.red, tc16s::red_bytes(h->nsm)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.ticket, sizeof(unsigned)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.perm, tc16s::perm_bytes(h->mcap)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.perm_tmp, tc16s::perm_bytes(h->mcap)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.keys, tc16s::perm_bytes(h->mcap)) == cudaSuccess;
     if (h->tc_refine) ok &= cudaMalloc(&h->dBdf, tc16r::bdf_bytes(h->ld, h->mcap)) == cudaSuccess;
   }
   ok &= dalloc(&h->dSt, 1) == cudaSuccess;

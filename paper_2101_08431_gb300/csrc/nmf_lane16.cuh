@@ -294,20 +294,6 @@ struct LaneNnls16 {
   }
 };
 
-// (G y)_a in FP64 on a 16-lane group: row a of G (lane a), y component c on lane base + c
-__device__ __forceinline__ double gdot64(const double* Grow, double y, unsigned gm, int base) {
-  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const double v = __shfl_sync(gm, y, base + c);
-    if ((c & 3) == 0) s0 = fmad(Grow[c], v, s0);
-    else if ((c & 3) == 1) s1 = fmad(Grow[c], v, s1);
-    else if ((c & 3) == 2) s2 = fmad(Grow[c], v, s2);
-    else s3 = fmad(Grow[c], v, s3);
-  }
-  return (s0 + s1) + (s2 + s3);
-}
-
 // ---------------------------------------------------------------------------
 // FP32-predicted, FP64-accurate solve of one 16-variable problem on a 16-lane
 // group.  An FP32 Lawson-Hanson solve (nf: its inverse of G_PP is carried
@@ -315,15 +301,32 @@ __device__ __forceinline__ double gdot64(const double* Grow, double y, unsigned 
 // iterative refinement x_P += inv(G_PP) (b - G x)_P -- the residual in FP64,
 // the correction through the FP32 inverse -- bring x to FP64 accuracy (each
 // step multiplies the error by ~2^-24 cond(G_PP)) until the correction is at
-// most rtol max|x| (at most maxit steps); x is accepted when the FP64
+// most rtol max|x| (at most maxit steps; with `converge`, a refinement that
+// has not reached rtol by then is not accepted).  x is accepted when the FP64
 // optimality test holds: x_P > 0 and no gradient b - G x above the entering
-// tolerance 10 k eps (max|b| + max G_aa max|x|) outside P.  G64: row a of G
-// in FP64 (lane a).  Returns true when accepted (x, *mask set); otherwise x
-// holds the refined point, a warm start for the FP64 solve.
+// tolerance 10 k eps (max|b| + max G_aa max|x|) outside P.  A variable the
+// test finds entering (the largest gradient, lowest index on ties) is added
+// to P through the FP32 inverse and x refined again, at most twice (the
+// FP32 solve's coarser tolerance leaves out such variables near an
+// optimum).  G64: row a of G in FP64 (lane a).  Returns true when accepted
+// (x, *mask set); otherwise x holds the refined point, a warm start for the
+// FP64 solve.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double resid64(const double* G64, double b, double x, unsigned gm, int base) {
+  double s0 = b, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 16; c += 4) {
+    s0 = fmad(-G64[c], __shfl_sync(gm, x, base + c), s0);
+    s1 = fmad(-G64[c + 1], __shfl_sync(gm, x, base + c + 1), s1);
+    s2 = fmad(-G64[c + 2], __shfl_sync(gm, x, base + c + 2), s2);
+    s3 = fmad(-G64[c + 3], __shfl_sync(gm, x, base + c + 3), s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 __device__ __forceinline__ bool predict_refine16(LaneNnls16<float>& nf, const double* G64, double gdiag_max, double b,
                                                  double& x, uint32_t* mask, int* status, bool warm, double eps,
-                                                 double rtol, int maxit) {
+                                                 double rtol, int maxit, bool converge) {
   constexpr int K = 16;
   float xv = (float)x;
   uint32_t P = 0;
@@ -331,35 +334,58 @@ __device__ __forceinline__ bool predict_refine16(LaneNnls16<float>& nf, const do
   *status = st;
   x = (double)xv;
   if (st != 0 || P != nf.Pc) return false;
-  const bool inP = (P >> nf.a) & 1u;
-  for (int it = 0; it < maxit; ++it) {
-    double rr = b;
+  double bmax = fabs(b);
 #pragma unroll
-    for (int c = 0; c < K; ++c) rr = fmad(-G64[c], __shfl_sync(nf.gm, x, nf.base + c), rr);
-    const float dz = nf.apply(P, (float)rr);
-    if (inP) x += (double)dz;
-    double dmax = inP ? fabs((double)dz) : 0.0, xmax = inP ? fabs(x) : 0.0;
+  for (int o = 8; o >= 1; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(nf.gm, bmax, o));
+  for (int round = 0; round < 3; ++round) {
+    const bool inP = (P >> nf.a) & 1u;
+    bool conv = false;
+    for (int it = 0; it < maxit; ++it) {
+      const double rr = resid64(G64, b, x, nf.gm, nf.base);
+      const float dz = nf.apply(P, (float)rr);
+      if (inP) x += (double)dz;
+      double dmax = inP ? fabs((double)dz) : 0.0, xmax = inP ? fabs(x) : 0.0;
+#pragma unroll
+      for (int o = 8; o >= 1; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(nf.gm, dmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(nf.gm, xmax, o));
+      }
+      if (dmax <= rtol * xmax) {
+        conv = true;
+        break;
+      }
+    }
+    if (converge && !conv) return false;                // G_PP too ill conditioned for the FP32 inverse
+    if (nf.gballot(inP && !(x > 0.0))) return false;   // infeasible: the FP64 solve decides
+    const double w = resid64(G64, b, x, nf.gm, nf.base);
+    double xmax = inP ? fabs(x) : 0.0;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(nf.gm, xmax, o));
+    const double tol = 10.0 * K * eps * (bmax + gdiag_max * xmax);
+    const bool cand = !inP && w > tol;
+    if (!nf.gballot(cand)) {
+      if (!inP) x = 0.0;
+      *mask = P;
+      return true;
+    }
+    if (round == 2) break;
+    // the largest entering gradient (lowest index on ties) joins P
+    double bw = cand ? w : -1.0;
+    int bi = cand ? nf.a : 99;
 #pragma unroll
     for (int o = 8; o >= 1; o >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(nf.gm, dmax, o));
-      xmax = fmax(xmax, __shfl_xor_sync(nf.gm, xmax, o));
+      const double ow = __shfl_xor_sync(nf.gm, bw, o);
+      const int oi = __shfl_xor_sync(nf.gm, bi, o);
+      if (ow > bw || (ow == bw && oi < bi)) {
+        bw = ow;
+        bi = oi;
+      }
     }
-    if (dmax <= rtol * xmax) break;
+    if (bi >= K || !nf.add(P, bi)) return false;
+    P |= 1u << bi;
+    nf.Pc = P;
   }
-  double w = b, xmax = inP ? fabs(x) : 0.0, bmax = fabs(b);
-#pragma unroll
-  for (int c = 0; c < K; ++c) w = fmad(-G64[c], __shfl_sync(nf.gm, x, nf.base + c), w);
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    bmax = fmax(bmax, __shfl_xor_sync(nf.gm, bmax, o));
-    xmax = fmax(xmax, __shfl_xor_sync(nf.gm, xmax, o));
-  }
-  const double tol = 10.0 * K * eps * (bmax + gdiag_max * xmax);
-  const bool bad = inP ? !(x > 0.0) : (w > tol);
-  if (!inP) x = 0.0;
-  if (((__ballot_sync(nf.gm, bad) >> nf.base) & 0xFFFFu) != 0) return false;
-  *mask = P;
-  return true;
+  return false;
 }
 
 }  // namespace nmfgb

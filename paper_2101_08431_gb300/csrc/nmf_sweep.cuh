@@ -1150,14 +1150,17 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
         // refinement gives x, and an FP64 optimality test accepts it;
         // otherwise the FP64 solve continues from the refined x
         LaneNnls16<float> nf;
-        nf.init(xs.HpF, 1.1920928955078125e-07f);
+        // the FP32 solve's tolerance constant: 2^-23 in the tensor-core pass
+        // (its P carries ~1e-5), 2^-27 in the incremental sweeps (above the
+        // FP32 rounding, close to the FP64 decisions)
+        nf.init(xs.HpF, p.inc ? 7.450580596923828e-09f : 1.1920928955078125e-07f);
         double hmax = 0.0;
 #pragma unroll
         for (int c = 0; c < K; ++c) hmax = dmax_nn(hmax, dabs(H[c * K + c]));
         done = p.inc ? predict_refine16(nf, H + a * K, hmax, pr, xn, &msk, &stt, warm, 5.684341886080802e-14,
-                                        1.4210854715202004e-14, 8)
+                                        1.4210854715202004e-14, 4, true)
                      : predict_refine16(nf, H + a * K, hmax, pr, xn, &msk, &stt, warm, Xs::EPS,
-                                        9.094947017729282e-13, 2);
+                                        9.094947017729282e-13, 2, false);
         warm = true;   // a fallback starts from the refined x
       }
       if (!done) {

@@ -13,6 +13,7 @@ namespace tc16s {
 size_t bpart_bytes(int mcap) { return (size_t)8 * (size_t)mcap * K * sizeof(float); }
 size_t xs_bytes(int ld) { return (size_t)ld * 64; }
 size_t ys_bytes(int mcap) { return (size_t)((mcap + PG_COLS - 1) / PG_COLS) * PG_COLS * 64; }
+size_t perm_bytes(int mcap) { return (size_t)mcap * sizeof(int); }
 size_t red_bytes(int nsm) { return (size_t)3 * (size_t)std::max(1, nsm) * RED * sizeof(double); }
 
 namespace {
@@ -118,8 +119,9 @@ cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, con
     bgemm_kernel<<<L.gridB, NT, L.smemB, s>>>(T.b, p, B, L);
     n += 2;
   }
+  sort_cols_kernel<<<1, SORT_T, 0, s>>>(p, B);
   solve_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, L, mode);
-  ++n;
+  n += 2;
   if (mode != MODE_KKT) {
     pgemm_kernel<<<L.gridP, NT, L.smemP, s>>>(T.p, p, B, L);
     ++n;
@@ -172,8 +174,9 @@ cudaError_t launch(const Problem& p, int mode, int pass, const RefPlan& R, const
       dfb_kernel<<<R.gridB, TB, dfb_smem(), s>>>(p, Bdf, R);
       ++n;
     }
+    tc16s::sort_cols_kernel<<<1, tc16s::SORT_T, 0, s>>>(p, B);
     solve64_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, Bdf, R, L.cpg, R.nrbB, R.SPd, REF, mode);
-    ++n;
+    n += 2;
     if (mode != MODE_KKT) {
       dfp_kernel<<<R.gridP, TP, 0, s>>>(p, R, mode);
       ++n;
@@ -183,9 +186,10 @@ cudaError_t launch(const Problem& p, int mode, int pass, const RefPlan& R, const
     const int tot = p.ld * K;
     xdsplit_kernel<<<std::min((tot + 255) / 256, 1024), 256, 0, s>>>(p, B);
     tc16s::bgemm_kernel<<<L.gridB, tc16s::NT, L.smemB, s>>>(T.b, p, B, L);
+    tc16s::sort_cols_kernel<<<1, tc16s::SORT_T, 0, s>>>(p, B);
     solve64_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, Bdf, R, L.cpg, L.SB, L.SP, INC, mode);
     tc16s::pgemm_kernel<<<L.gridP, tc16s::NT, L.smemP, s>>>(T.p, p, B, L);
-    n += 4;
+    n += 5;
   }
   if (nl) *nl = n;
   return cudaGetLastError();

@@ -26,6 +26,9 @@ struct Bufs {
   unsigned char* Ys;          // split of Y: one block of 512 bytes per 8 window columns
   double* red;                // [gridS][16 * 16 + NYT] block partials of the solve kernel
   unsigned* ticket;           // last-block ticket of the solve kernel (self-resetting)
+  int* perm;                  // [mcap] window columns in the order of their passive sets
+  int* perm_tmp;              // [mcap] the order after the first radix pass
+  int* keys;                  // [mcap] passive-set mask of each window column
 };
 
 struct Plan {
@@ -47,6 +50,8 @@ size_t bpart_bytes(int mcap);
 size_t xs_bytes(int ld);
 size_t ys_bytes(int mcap);
 size_t red_bytes(int nsm);
+// the three column-order arrays (perm, perm_tmp, keys), each of this size
+size_t perm_bytes(int mcap);
 // false when the driver entry point is missing or rejects the shape
 bool encode_maps(void* M, int ld, int mcap, Maps* out);
 // Plan for ld rows and m resident columns (host arithmetic only); false if

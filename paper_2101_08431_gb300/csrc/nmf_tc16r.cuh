@@ -23,7 +23,8 @@
 //              chunk of columns in shared memory (hi/lo pairs, broadcast
 //              reads); FP64 partials into Ppart[split][row]
 // solve64_kernel  the FP64 column solves of both kinds (16-lane groups on
-//              consecutive columns, carried inverse), FP64 KKT terms and H,
+//              runs of columns ordered by passive set, carried inverse), FP64
+//              KKT terms and H,
 //              the records, and the split of Y - Y_ref for the incremental
 //              P-GEMM
 #pragma once
@@ -167,32 +168,22 @@ __global__ void __launch_bounds__(TP) dfp_kernel(Problem p, RefPlan R, int mode)
 // ---------------------------------------------------------------------------
 enum Kind { REF = 0, INC = 1 };
 
-__global__ void __launch_bounds__(SOLVE_T, 1) solve64_kernel(Problem p, tc16s::Bufs bf, const double* Bdf,
+__global__ void __launch_bounds__(SOLVE_T, 2) solve64_kernel(Problem p, tc16s::Bufs bf, const double* Bdf,
                                                              RefPlan R, int cpg, int nbpart, int Q, int kind,
                                                              int mode) {
   __shared__ double Gd[K][K + 1];
-  __shared__ float Gf[K][K + 1];
   __shared__ double wred[SOLVE_T / 32][tc16s::RED];
   __shared__ unsigned last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   DevState* st = p.st;
   if (st->done) return;
   const int cur = st->iter & 1, nxt = cur ^ 1;
-  for (int e = tid; e < K * K; e += SOLVE_T) {
-    Gd[e / K][e % K] = p.G[e];
-    Gf[e / K][e % K] = (float)p.G[e];
-  }
+  for (int e = tid; e < K * K; e += SOLVE_T) Gd[e / K][e % K] = p.G[e];
   __syncthreads();
-  // FP32-predicted, FP64-refined solves (predict_refine16; the FP32 solver
-  // carries its inverse along the group's consecutive columns), the FP64
-  // solve where the prediction fails; the tolerance constant of the
-  // compensated contractions, 2^-44
-  LaneNnls16<float> nf;
-  nf.init(Gf, 1.1920928955078125e-07f);
-  double gdmax = 0.0;
-#pragma unroll
-  for (int c = 0; c < K; ++c) gdmax = dmax_nn(gdmax, dabs(Gd[c][c]));
-  const int a = nf.a;
+  LaneNnls16<double> nn;
+  // FP64 solves with the tolerance constant of the compensated contractions
+  nn.init(Gd, 5.684341886080802e-14);
+  const int a = nn.a;
   const int ncols = p.m, ncolp = (ncols + tc16s::PG_COLS - 1) / tc16s::PG_COLS * tc16s::PG_COLS;
   const int gid = blockIdx.x * (SOLVE_T / 16) + (tid >> 4);
   const int cbeg = min(ncolp, gid * cpg), cend = min(ncolp, cbeg + cpg);
@@ -203,14 +194,15 @@ __global__ void __launch_bounds__(SOLVE_T, 1) solve64_kernel(Problem p, tc16s::B
   double hacc[9];   // lane a: H[a][(a + d) % 16], d = 0..8
 #pragma unroll
   for (int d = 0; d < 9; ++d) hacc[d] = 0.0;
-  for (int col = cbeg; col < cend; ++col) {
-    if (col >= ncols) {
+  for (int ci = cbeg; ci < cend; ++ci) {
+    if (ci >= ncols) {
       if (inc && mode != MODE_KKT) {
-        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, a)) = 0;
-        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, K + a)) = 0;
+        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(ci, a)) = 0;
+        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(ci, K + a)) = 0;
       }
       continue;
     }
+    const int col = bf.perm[ci];   // columns in the order of their passive sets (sort_cols_kernel)
     const int phys = wrap_col(p.head, col, p.mcap);
     const double yo = p.Y[cur][(size_t)phys * K + a];
     const uint32_t om = p.ymask[cur][phys];
@@ -227,16 +219,10 @@ __global__ void __launch_bounds__(SOLVE_T, 1) solve64_kernel(Problem p, tc16s::B
     double yn = yo;
     uint32_t msk = 0;
     int stt = 0;
-    if (mode == MODE_SWEEP &&
-        !predict_refine16(nf, &Gd[a][0], gdmax, b, yn, &msk, &stt, p.warm != 0, 5.684341886080802e-14,
-                          1.4210854715202004e-14, 8)) {
-      LaneNnls16<double> nn;
-      nn.init(Gd, 5.684341886080802e-14);
-      stt = nn.solve(b, yn, true, &msk);
-    }
+    if (mode == MODE_SWEEP) stt = nn.solve(b, yn, p.warm != 0, &msk);
     if (mode != MODE_PRIME) {
       // Y-half KKT terms of the incoming iterate: g = G yo - b (component a)
-      const double gy = gdot64(&Gd[a][0], yo, nf.gm, nf.base) - b;
+      const double gy = nn.gdot(yo) - b;
       const double mn = dminz(gy), pos = dmaxz(gy) * yo;
       acc_t[YT_NEG] = fmad(mn, mn, acc_t[YT_NEG]);
       acc_t[YT_COMP] = fmad(pos, pos, acc_t[YT_COMP]);
@@ -260,12 +246,12 @@ __global__ void __launch_bounds__(SOLVE_T, 1) solve64_kernel(Problem p, tc16s::B
         p.Yref[(size_t)phys * K + a] = yn;
       }
     } else if (mode == MODE_PRIME) {
-      const uint32_t pm = (__ballot_sync(nf.gm, dpos(yo)) >> nf.base) & 0xFFFFu;
+      const uint32_t pm = (__ballot_sync(nn.gm, dpos(yo)) >> nn.base) & 0xFFFFu;
       if (a == 0) p.ymask[cur][phys] = pm;
     }
     if (mode != MODE_KKT) {
 #pragma unroll
-      for (int d = 0; d < 9; ++d) hacc[d] = fmad(yn, __shfl_sync(nf.gm, yn, nf.base + ((a + d) & 15)), hacc[d]);
+      for (int d = 0; d < 9; ++d) hacc[d] = fmad(yn, __shfl_sync(nn.gm, yn, nn.base + ((a + d) & 15)), hacc[d]);
       if (inc) {   // the change of y since the reference, split for the P-GEMM
         const float dy = __double2float_rn(yn - p.Yref[(size_t)phys * K + a]);
         const uint16_t h = tc16s::bf16_bits(dy);

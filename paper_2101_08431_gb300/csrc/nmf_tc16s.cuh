@@ -592,9 +592,82 @@ __global__ void __launch_bounds__(NT, 2) pgemm_kernel(const __grid_constant__ CU
 }
 
 // ---------------------------------------------------------------------------
-// Column solves: every 16-lane group takes a contiguous range of window
-// columns (neighbouring columns share most of their passive set, so the
-// carried inverse of the group is reused), b_j = sum of the SB partials
+// Column order for the solves: the window's columns stably sorted by their
+// current passive set (16-bit mask), so that a 16-lane group's consecutive
+// columns share their passive set and its carried inverse of G_PP is reused
+// (the factorization reuse of Sec. 2, over columns grouped by passive set
+// instead of neighbouring ones).  One CTA: the keys are gathered, then two
+// LSD radix passes of 8 bits; each warp sorts a contiguous segment, lanes
+// rank equal digits with a match, so equal keys keep their window order.
+// ---------------------------------------------------------------------------
+constexpr int SORT_T = 1024;
+
+__global__ void __launch_bounds__(SORT_T) sort_cols_kernel(Problem p, Bufs bf) {
+  __shared__ unsigned hist[SORT_T / 32][256];
+  __shared__ unsigned dtot[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (p.st->done) return;
+  const int cur = p.st->iter & 1;
+  const int m = p.m;
+  for (int i = tid; i < m; i += SORT_T) bf.keys[i] = (int)(p.ymask[cur][wrap_col(p.head, i, p.mcap)] & 0xFFFFu);
+  __syncthreads();
+  const int seg = (m + SORT_T / 32 - 1) / (SORT_T / 32);
+  const int s0 = min(m, warp * seg), s1 = min(m, s0 + seg);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int* src = pass == 0 ? nullptr : bf.perm_tmp;
+    int* dst = pass == 0 ? bf.perm_tmp : bf.perm;
+    const int shift = 8 * pass;
+    for (int e = tid; e < (SORT_T / 32) * 256; e += SORT_T) hist[e >> 8][e & 255] = 0u;
+    __syncthreads();
+    for (int base = s0; base < s1; base += 32) {   // digit counts of the warp's segment
+      const int i = base + lane;
+      const bool v = i < s1;
+      const int col = v ? (src ? src[i] : i) : 0;
+      const unsigned d = v ? ((unsigned)bf.keys[col] >> shift) & 255u : 256u + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (v && (peers & lt) == 0) hist[warp][d] += (unsigned)__popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    if (tid < 256) {   // offsets: digit-major, then warp order
+      unsigned t = 0;
+      for (int w = 0; w < SORT_T / 32; ++w) {
+        const unsigned c = hist[w][tid];
+        hist[w][tid] = t;
+        t += c;
+      }
+      dtot[tid] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned t = 0;
+      for (int d = 0; d < 256; ++d) {
+        const unsigned c = dtot[d];
+        dtot[d] = t;
+        t += c;
+      }
+    }
+    __syncthreads();
+    for (int base = s0; base < s1; base += 32) {   // stable scatter
+      const int i = base + lane;
+      const bool v = i < s1;
+      const int col = v ? (src ? src[i] : i) : 0;
+      const unsigned d = v ? ((unsigned)bf.keys[col] >> shift) & 255u : 256u + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (v) dst[dtot[d] + hist[warp][d] + (unsigned)__popc(peers & lt)] = col;
+      __syncwarp();
+      if (v && (peers & lt) == 0) hist[warp][d] += (unsigned)__popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column solves: every 16-lane group takes a contiguous range of the columns
+// ordered by passive set (sort_cols_kernel: the carried inverse of the group
+// is reused along it), b_j = sum of the SB partials
 // (fixed order); the KKT terms of the incoming iterate and H = Y Y^T; the
 // BF16 split of the new y for the P-GEMM (zero for the padding columns of the
 // last 64-column granule).  This pass's b carries ~1e-5 relative error, so
@@ -628,14 +701,15 @@ __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, P
   float hacc[9];   // lane a: H[a][(a + d) % 16], d = 0..8
 #pragma unroll
   for (int d = 0; d < 9; ++d) hacc[d] = 0.f;
-  for (int col = cbeg; col < cend; ++col) {
-    if (col >= ncols) {
+  for (int ci = cbeg; ci < cend; ++ci) {
+    if (ci >= ncols) {
       if (mode != MODE_KKT) {
-        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, a)) = 0;
-        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, K + a)) = 0;
+        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(ci, a)) = 0;
+        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(ci, K + a)) = 0;
       }
       continue;
     }
+    const int col = bf.perm[ci];   // columns in the order of their passive sets
     const int phys = wrap_col(p.head, col, p.mcap);
     const float yo = (float)p.Y[cur][(size_t)phys * K + a];
     const uint32_t om = p.ymask[cur][phys];
