@@ -119,9 +119,8 @@ cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, con
     bgemm_kernel<<<L.gridB, NT, L.smemB, s>>>(T.b, p, B, L);
     n += 2;
   }
-  sort_cols_kernel<<<1, SORT_T, 0, s>>>(p, B);
   solve_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, L, mode);
-  n += 2;
+  ++n;
   if (mode != MODE_KKT) {
     pgemm_kernel<<<L.gridP, NT, L.smemP, s>>>(T.p, p, B, L);
     ++n;

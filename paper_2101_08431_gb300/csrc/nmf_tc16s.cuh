@@ -665,9 +665,11 @@ __global__ void __launch_bounds__(SORT_T) sort_cols_kernel(Problem p, Bufs bf) {
 }
 
 // ---------------------------------------------------------------------------
-// Column solves: every 16-lane group takes a contiguous range of the columns
-// ordered by passive set (sort_cols_kernel: the carried inverse of the group
-// is reused along it), b_j = sum of the SB partials
+// Column solves: every 16-lane group takes a contiguous range of window
+// columns (the carried inverse of the group is reused where neighbours share
+// their passive set; the FP32 rebuild is cheap enough that sorting the
+// columns by passive set, as the FP64 refinement solves do, does not pay
+// here), b_j = sum of the SB partials
 // (fixed order); the KKT terms of the incoming iterate and H = Y Y^T; the
 // BF16 split of the new y for the P-GEMM (zero for the padding columns of the
 // last 64-column granule).  This pass's b carries ~1e-5 relative error, so
@@ -701,15 +703,14 @@ __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, P
   float hacc[9];   // lane a: H[a][(a + d) % 16], d = 0..8
 #pragma unroll
   for (int d = 0; d < 9; ++d) hacc[d] = 0.f;
-  for (int ci = cbeg; ci < cend; ++ci) {
-    if (ci >= ncols) {
+  for (int col = cbeg; col < cend; ++col) {
+    if (col >= ncols) {
       if (mode != MODE_KKT) {
-        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(ci, a)) = 0;
-        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(ci, K + a)) = 0;
+        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, a)) = 0;
+        *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, K + a)) = 0;
       }
       continue;
     }
-    const int col = bf.perm[ci];   // columns in the order of their passive sets
     const int phys = wrap_col(p.head, col, p.mcap);
     const float yo = (float)p.Y[cur][(size_t)phys * K + a];
     const uint32_t om = p.ymask[cur][phys];
