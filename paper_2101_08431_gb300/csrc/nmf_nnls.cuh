@@ -615,6 +615,69 @@ __device__ void build_subset_table_lanes(const NnlsSolver<K>& S, double* tab, in
   build_subset_table_lanes_v<K, double>(S.G, S.pivot_min, tab, ok, t0, nthreads, sync);
 }
 
+// The subset table with every subset independent of the others: a group of
+// KP lanes takes a subset P and inverts G_PP by Gauss-Jordan elimination in
+// ascending index order (lane a holds row a of [G_PP | I]); the pivots are
+// the Schur complements the bordering method tests, so the degenerate
+// entries are the same, and the dependency chain is |P| pivot steps instead
+// of k levels of bordering (a subset's inverse does not wait for its
+// parent's).  For small k, where all 2^k - 1 subsets fit the groups of one
+// round.  Called by the `nthreads` threads starting at thread t0 (multiples
+// of 32); needs no barrier of its own.
+template <int K>
+__device__ void build_subset_table_gj(const double* Gm, double pivot_min, double* tab, int* ok, int t0,
+                                      int nthreads) {
+  static_assert(K <= 8, "subset tables are built for k <= 8");
+  constexpr int NC = (1 << K) - 1;
+  LaneGroup<K> g;
+  g.init();
+  const int local = (int)threadIdx.x - t0;
+  const int group = local / LaneGroup<K>::KP, ngroups = nthreads / LaneGroup<K>::KP;
+  const int nrounds = (NC + ngroups - 1) / ngroups;
+#pragma unroll 1
+  for (int rd = 0; rd < nrounds; ++rd) {   // rounds are warp-uniform: every lane runs every round
+    const int task = rd * ngroups + group;
+    const bool valid = task < NC;
+    const uint32_t P = valid ? (uint32_t)(task + 1) : 1u;
+    const bool ina = g.a < K && ((P >> g.a) & 1u);
+    double R[K], I[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      R[c] = (ina && ((P >> c) & 1u)) ? Gm[g.a * K + c] : 0.0;
+      I[c] = (ina && c == g.a) ? 1.0 : 0.0;
+    }
+    bool good = true;
+#pragma unroll
+    for (int pv = 0; pv < K; ++pv) {
+      // every lane of the warp runs every pivot step (the shuffles are
+      // full-warp); a step whose index is not in the group's P changes nothing
+      const bool inpv = (P >> pv) & 1u;
+      const double piv = g.from(R[pv], pv);
+      if (inpv) good = good && piv > pivot_min;
+      const double rinv = VOps<double>::rcp(inpv ? piv : 1.0);
+      const double f = R[pv] * rinv;   // this row's multiple of the pivot row
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double rp = g.from(R[c], pv), ip = g.from(I[c], pv);
+        if (inpv && g.a == pv) {
+          R[c] *= rinv;
+          I[c] *= rinv;
+        } else if (inpv && ina) {
+          R[c] = fmad(-f, rp, R[c]);
+          I[c] = fmad(-f, ip, I[c]);
+        }
+      }
+    }
+    if (valid && g.a < K) {
+      double* D = tab + (size_t)P * K * K + g.a * K;
+#pragma unroll
+      for (int c = 0; c < K; ++c) D[c] = ina ? I[c] : 0.0;
+    }
+    if (valid && g.a == 0) ok[P] = good ? 1 : 0;
+  }
+  if (local == 0) ok[0] = 1;
+}
+
 // Solve the columns held by the warp.  Per lane: b = component a of the
 // right-hand side, y = component a of the warm start (in) / solution (out),
 // grow = row a of G (K values, registers).  tab / ok: subset table of G.

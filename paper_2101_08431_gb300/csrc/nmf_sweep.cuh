@@ -690,6 +690,39 @@ __device__ __forceinline__ void ypass_body(const Problem& p, int mode, int S, in
 // Called by the 32 lanes of one warp: the six square roots and three quotients run on
 // separate lanes (each FP64 warp instruction costs the same whatever the
 // number of active lanes); lane 0 writes out[].  dx2 < 0: no step term.
+// sqrt(x) and a / b to ~2^-23 relative: the significands in FP32, the
+// binary exponents exactly (FP64 square roots and divisions are chains of
+// ~20 dependent FP64 instructions on this part, and these ratios and norms
+// of the statistics record need 7 digits at most).  Outside the normal FP64
+// range, for non-positive or non-finite arguments, the FP64 operation.
+__device__ __forceinline__ bool normal_pos(double x, int& e, double& m) {
+  const long long b = __double_as_longlong(x);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (b <= 0 || be == 0 || be >= 2046) return false;   // <= 0, denormal, huge, inf or NaN
+  e = be - 1023;
+  m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | (1023ll << 52));   // [1, 2)
+  return true;
+}
+__device__ __forceinline__ double scale2(double v, int e) {   // v * 2^e for a normal result
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)e << 52));
+}
+__device__ __forceinline__ double sqrt_f32(double x) {
+  int e;
+  double m;
+  if (!normal_pos(x, e, m)) return sqrt(x);
+  if (e & 1) {   // make the exponent even: m in [2, 4)
+    m *= 2.0;
+    e -= 1;
+  }
+  return scale2((double)sqrtf((float)m), e / 2);
+}
+__device__ __forceinline__ double div_f32(double a, double b) {
+  int ea, eb;
+  double ma, mb;
+  if (!normal_pos(a, ea, ma) || !normal_pos(b, eb, mb)) return a / b;
+  return scale2((double)__fdiv_rn((float)ma, (float)mb), ea - eb);
+}
+
 __device__ inline void combine_stats_warp(const double* yterm, const double* xterm, double msq,
                                           double dx2, int iter, int fp64, double* out) {
   const int lane = threadIdx.x & 31;
@@ -702,7 +735,7 @@ __device__ inline void combine_stats_warp(const double* yterm, const double* xte
   else if (lane == 3) arg = yterm[YT_BNORM2];
   else if (lane == 4) arg = dx2 >= 0.0 ? dx2 + yterm[YT_DY2] : 0.0;
   else if (lane == 5) arg = xterm[XT_XNORM2] + yterm[YT_YNORM2];
-  const double sq = sqrt(arg);
+  const double sq = arg > 0.0 ? sqrt_f32(arg) : 0.0;
   const double e1 = __shfl_sync(0xffffffffu, sq, 0), e2 = __shfl_sync(0xffffffffu, sq, 1);
   const double sg = __shfl_sync(0xffffffffu, sq, 2) + __shfl_sync(0xffffffffu, sq, 3);
   const double s4 = __shfl_sync(0xffffffffu, sq, 4), s5 = __shfl_sync(0xffffffffu, sq, 5);
@@ -710,7 +743,7 @@ __device__ inline void combine_stats_warp(const double* yterm, const double* xte
   const double d2 = sg * xymax;
   const double num = lane == 0 ? e1 : (lane == 1 ? e2 : s4);
   const double den = lane == 0 ? sg : (lane == 1 ? d2 : 1.0 + s5);
-  const double qt = (lane >= 2 || den > 0.0) ? num / den : num;
+  const double qt = (lane >= 2 || den > 0.0) ? (num > 0.0 ? div_f32(num, den) : 0.0) : num;
   const double r1 = __shfl_sync(0xffffffffu, qt, 0), r2 = __shfl_sync(0xffffffffu, qt, 1);
   const double step = __shfl_sync(0xffffffffu, qt, 2);
   if (lane != 0) return;
@@ -742,13 +775,13 @@ struct XTraits {
 };
 
 // Sum over p of src[p * stride + e] for e < nval, in a fixed order, with
-// short FP64 dependency chains: 8 threads per value each add every 8th term,
-// then a 3-level shuffle tree inside the 8-lane group.  Called by all T
+// short FP64 dependency chains: G threads per value (8 by default) each add
+// every G-th term, then a shuffle tree inside the G-lane group.  Called by all T
 // threads of the block; writes out[e] (shared memory).  max_e: 1 = max.
-template <int T>
+template <int T, int G = 8>
 __device__ void tree_sum(const double* src, int nparts, size_t stride, int nval, double* out,
                          int max_e) {
-  constexpr int G = 8, VPB = T / G, U = 8;   // U loads in flight per thread
+  constexpr int VPB = T / G, U = 8;   // U loads in flight per thread
   const int g = threadIdx.x & (G - 1), vi = threadIdx.x / G;
   for (int e0 = 0; e0 < nval; e0 += VPB) {
     const int e = e0 + vi;
@@ -840,7 +873,12 @@ struct XSmem {
     return v;
   }
   static constexpr int WT_NEED = (binom_mid() * LaneGroup<K>::KP + 31) / 32;
-  static constexpr int WT = TABLE ? (WT_NEED < 1 ? 1 : (WT_NEED > Tr::NW / 2 ? Tr::NW / 2 : WT_NEED)) : 0;
+  // k <= 5: the table by independent Gauss-Jordan inversions, every subset
+  // in one round (build_subset_table_gj); larger k: level by level
+  static constexpr bool GJ = K <= 5;
+  static constexpr int WT_GJ = (((1 << K) - 1) * LaneGroup<K>::KP + 31) / 32;
+  static constexpr int WT = !TABLE ? 0 : GJ ? WT_GJ
+                                            : (WT_NEED < 1 ? 1 : (WT_NEED > Tr::NW / 2 ? Tr::NW / 2 : WT_NEED));
   // value type of the row solves: FP64 in every pass (see YTraits::F32NN)
   static constexpr bool F32NN = false;
   using SV = typename std::conditional<F32NN, float, double>::type;
@@ -917,7 +955,8 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   if (hglob) {
     for (int e = tid; e < K * K; e += T) H[e] = p.Hg[e];
   } else {
-    tree_sum<T>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
+    // as many threads per value as the block has for K * K values (one load each for ~Q / 32 partials)
+    tree_sum<T, (K * K * 32 <= T) ? 32 : ((K * K * 16 <= T) ? 16 : 8)>(p.Hpart, Q, (size_t)K * K, K * K, H, -1);
   }
   // the first wt warps build the subset table of H while the others sum the
   // cluster partials of P
@@ -933,6 +972,8 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
         named_sync(2, wt * 32);
         build_subset_table_lanes_v<K, SV>(xs.Hn, (SV)ts.pivot_min, tab, tok, 0, wt * 32,
                                           [wt] { named_sync(2, wt * 32); });
+      } else if constexpr (Xs::GJ) {
+        build_subset_table_gj<K>(H, ts.pivot_min, tab, tok, 0, wt * 32);
       } else {
         build_subset_table_lanes<K>(ts, tab, tok, 0, wt * 32, [wt] { named_sync(2, wt * 32); });
       }
@@ -1266,7 +1307,8 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       if (gbuilt) {
         NnlsSolver<K> gs;
         gs.init(Gs, 2.220446049250313e-16);
-        build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 32, T - 32, [] { named_sync(3, T - 32); });
+        if constexpr (Xs::GJ) build_subset_table_gj<K>(Gs, gs.pivot_min, p.Gtab, p.Gok, 32, T - 32);
+        else build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 32, T - 32, [] { named_sync(3, T - 32); });
       }
     }
   }
