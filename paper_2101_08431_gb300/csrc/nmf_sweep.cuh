@@ -1307,8 +1307,9 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
       if (gbuilt) {
         NnlsSolver<K> gs;
         gs.init(Gs, 2.220446049250313e-16);
-        if constexpr (Xs::GJ) build_subset_table_gj<K>(Gs, gs.pivot_min, p.Gtab, p.Gok, 32, T - 32);
-        else build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 32, T - 32, [] { named_sync(3, T - 32); });
+        // level by level: the warps without a subset of a level skip its
+        // arithmetic, so the FP64 pipe stays free for the statistics on warp 0
+        build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 32, T - 32, [] { named_sync(3, T - 32); });
       }
     }
   }
