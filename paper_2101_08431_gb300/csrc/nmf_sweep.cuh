@@ -1298,10 +1298,52 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   const bool gbuilt = TABLE && (K > 6 || p.tab_global || p.gtab_tail);
   double rec[NSTAT];
   if (warp == 0) {
+    // the statistics and the record of the iterate (warp 0) while warps 1..15
+    // build the table of G: the record does not wait for the table (the next
+    // kernel, or the release of the batch's tail flag below, follows both)
     if (mode != MODE_PRIME)
       // statistics of iterate t: Y half from this sweep's M pass, X half from
       // the sweep that produced X_t
       combine_stats_warp(yfin, st->xiter[cur], st->msq, fin[K * K + XT_DX2], iter, p.fp64_pass, rec);
+    if (lane == 0) {
+      st->gtab_valid = gbuilt ? 1 : 0;
+      double xt[NXT];
+      for (int e = 0; e < NXT; ++e) xt[e] = fin[K * K + e];
+      xt[XT_VALID] = 1.0;
+      if (mode == MODE_PRIME) {
+        for (int e = 0; e < NXT; ++e) st->xiter[cur][e] = xt[e];
+      } else {
+        rec[ST_CHANGED_ROWS] = fin[K * K + XT_CHANGED];
+        rec[ST_NOTCONV] += fin[K * K + XT_NOTCONV];
+        const bool kkt_ok = rec[ST_VALID] > 0.0 && ((p.kkt_target > 0.0 && rec[ST_REL] <= p.kkt_target) ||
+                                                    (p.kkt_abs_target > 0.0 && rec[ST_EABS] <= p.kkt_abs_target));
+        const bool step_ok = p.stol > 0.0 && rec[ST_STEP] >= 0.0 && rec[ST_STEP] <= p.stol;
+        if (kkt_ok) {
+          st->done = 1;
+          st->stop_reason = 1;
+        } else {
+          st->iter = iter + 1;
+          if (step_ok) {
+            st->done = 1;
+            st->stop_reason = 2;
+          }
+        }
+        for (int e = 0; e < NSTAT; ++e) st->stats[iter % STAT_CAP][e] = rec[e];
+        for (int e = 0; e < NXT; ++e) st->xiter[nxt][e] = xt[e];
+        if (p.fp64_pass) ++st->fp64_sweeps;
+        if (p.auto_mixed && st->pass_var != VAR_DF && rec[ST_VALID] > 0.0) {
+          const double rel = rec[ST_REL];
+          if (st->best_rel <= 0.0 || rel < 0.98 * st->best_rel) {   // <= 0: none yet
+            st->best_rel = rel;
+            st->since_best = 0;
+          } else {
+            ++st->since_best;
+          }
+          if (rel <= p.mixed_switch || st->since_best >= p.stall_sweeps) st->pass_var = VAR_DF;
+        }
+      }
+      st->xblocks_done = 0;
+    }
   } else {
     if constexpr (TABLE) {
       if (gbuilt) {
@@ -1312,47 +1354,6 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
         build_subset_table_lanes<K>(gs, p.Gtab, p.Gok, 32, T - 32, [] { named_sync(3, T - 32); });
       }
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    st->gtab_valid = gbuilt ? 1 : 0;
-    double xt[NXT];
-    for (int e = 0; e < NXT; ++e) xt[e] = fin[K * K + e];
-    xt[XT_VALID] = 1.0;
-    if (mode == MODE_PRIME) {
-      for (int e = 0; e < NXT; ++e) st->xiter[cur][e] = xt[e];
-    } else {
-      rec[ST_CHANGED_ROWS] = fin[K * K + XT_CHANGED];
-      rec[ST_NOTCONV] += fin[K * K + XT_NOTCONV];
-      for (int e = 0; e < NSTAT; ++e) st->stats[iter % STAT_CAP][e] = rec[e];
-      for (int e = 0; e < NXT; ++e) st->xiter[nxt][e] = xt[e];
-      if (p.fp64_pass) ++st->fp64_sweeps;
-      if (p.auto_mixed && st->pass_var != VAR_DF && rec[ST_VALID] > 0.0) {
-        const double rel = rec[ST_REL];
-        if (st->best_rel <= 0.0 || rel < 0.98 * st->best_rel) {   // <= 0: none yet
-          st->best_rel = rel;
-          st->since_best = 0;
-        } else {
-          ++st->since_best;
-        }
-        if (rel <= p.mixed_switch || st->since_best >= p.stall_sweeps) st->pass_var = VAR_DF;
-      }
-      const bool kkt_ok = rec[ST_VALID] > 0.0 && ((p.kkt_target > 0.0 && rec[ST_REL] <= p.kkt_target) ||
-                                                  (p.kkt_abs_target > 0.0 && rec[ST_EABS] <= p.kkt_abs_target));
-      const bool step_ok = p.stol > 0.0 && rec[ST_STEP] >= 0.0 && rec[ST_STEP] <= p.stol;
-      if (kkt_ok) {
-        st->done = 1;
-        st->stop_reason = 1;
-      } else {
-        st->iter = iter + 1;
-        if (step_ok) {
-          st->done = 1;
-          st->stop_reason = 2;
-        }
-      }
-    }
-    st->xblocks_done = 0;
-    __threadfence();
   }
   if (tail_done) {
     __syncthreads();
