@@ -19,12 +19,20 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 __device__ __forceinline__ float bf16_val(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
-// hi/lo split of two FP32 values, packed two BF16 per word
+// two FP32 values rounded to nearest-even BF16 by one packed conversion:
+// a in the low half of the word, b in the high half
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+// hi/lo split of two FP32 values, packed two BF16 per word (a in the low
+// halves): hi = bf16(v), lo = bf16(v - hi), the subtraction exact in FP32.
+// Two packed conversions per pair: the scalar form's four conversions paced
+// the GEMM kernels' converter warps.
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const uint16_t ha = bf16_bits(a), hb = bf16_bits(b);
-  const uint16_t la = bf16_bits(a - bf16_val(ha)), lb = bf16_bits(b - bf16_val(hb));
-  hi = (uint32_t)ha | ((uint32_t)hb << 16);
-  lo = (uint32_t)la | ((uint32_t)lb << 16);
+  hi = bf16x2_bits(a, b);
+  lo = bf16x2_bits(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bound of every wait: 2 s of wall time
