@@ -766,7 +766,7 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
     ok &= cudaMalloc(&h->tcb.Xs, tc16s::xs_bytes(h->ld)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.Ys, tc16s::ys_bytes(h->mcap)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.red, tc16s::red_bytes(h->nsm)) == cudaSuccess;
-    ok &= cudaMalloc(&h->tcb.ticket, sizeof(unsigned)) == cudaSuccess;
+    ok &= cudaMalloc(&h->tcb.ticket, tc16s::ticket_count(h->nsm) * sizeof(unsigned)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.perm, tc16s::perm_bytes(h->mcap)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.perm_tmp, tc16s::perm_bytes(h->mcap)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.keys, tc16s::perm_bytes(h->mcap)) == cudaSuccess;
@@ -784,7 +784,7 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   cudaMemsetAsync(h->dM, 0, (size_t)h->ld * (h->mcap + h->mirror) * (h->store_f32 ? 4 : 8), h->stream);
   cudaMemsetAsync(h->dSt, 0, sizeof(DevState), h->stream);
   if (h->tc16) {
-    cudaMemsetAsync(h->tcb.ticket, 0, sizeof(unsigned), h->stream);
+    cudaMemsetAsync(h->tcb.ticket, 0, tc16s::ticket_count(h->nsm) * sizeof(unsigned), h->stream);
     if (!tc16s::encode_maps(h->dM, h->ld, h->mcap, &h->tcmaps)) return bail(NMF_ECUDA, "tensor maps of M rejected");
   }
   cudaMemsetAsync(h->dColsq, 0, sizeof(double) * h->mcap, h->stream);

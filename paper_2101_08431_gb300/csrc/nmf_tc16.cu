@@ -14,7 +14,12 @@ size_t bpart_bytes(int mcap) { return (size_t)8 * (size_t)mcap * K * sizeof(floa
 size_t xs_bytes(int ld) { return (size_t)ld * 64; }
 size_t ys_bytes(int mcap) { return (size_t)((mcap + PG_COLS - 1) / PG_COLS) * PG_COLS * 64; }
 size_t perm_bytes(int mcap) { return (size_t)mcap * sizeof(int); }
-size_t red_bytes(int nsm) { return (size_t)3 * (size_t)std::max(1, nsm) * RED * sizeof(double); }
+// block partials of up to 3 nsm blocks, their group partials, the totals
+size_t red_bytes(int nsm) {
+  const size_t nb = (size_t)3 * (size_t)std::max(1, nsm);
+  return (nb + (nb + RGROUP - 1) / RGROUP + 1) * RED * sizeof(double);
+}
+size_t ticket_count(int nsm) { return 1 + ((size_t)3 * (size_t)std::max(1, nsm) + RGROUP - 1) / RGROUP; }
 
 namespace {
 
@@ -98,13 +103,20 @@ bool plan(int ld, int m, int nsm, int smem_optin, Plan* out) {
   L.gridP = std::min(nrb * L.SP, slots);
   // column solves: a group's columns run in sequence, each from the inverse
   // of G_PP carried from its left neighbour (neighbouring columns share most
-  // of their passive set), so a group takes several columns: about one
-  // 16-group block per SM, at most 16 columns per group
+  // of their passive set), so a group takes several columns, at most 16.
   const int ncolp = ncg * PG_COLS;
-  L.cpg = std::max(1, std::min(16, (ncolp + nsm * (SOLVE_T / 16) - 1) / (nsm * (SOLVE_T / 16))));
-  const int ngroups = (ncolp + L.cpg - 1) / L.cpg;
-  L.gridS = (ngroups + SOLVE_T / 16 - 1) / (SOLVE_T / 16);
-  if (L.gridS > 3 * nsm) return false;
+  const auto groups = [&](int per_sm, int& cpg, int& grid) {
+    cpg = std::max(1, std::min(16, (ncolp + per_sm * nsm * (SOLVE_T / 16) - 1) / (per_sm * nsm * (SOLVE_T / 16))));
+    const int ngroups = (ncolp + cpg - 1) / cpg;
+    grid = (ngroups + SOLVE_T / 16 - 1) / (SOLVE_T / 16);
+  };
+  // FP64 refinement solves (solve64_kernel: FP64-pipe bound, runs of equal
+  // passive sets after the sort) one block per SM; the FP32 solves two: their
+  // chains of shuffles are latency-bound, and twice the groups with half the
+  // columns each measured 8 % faster at m = 16384 (three per SM: the same)
+  groups(1, L.cpg, L.gridS);
+  groups(2, L.cpgF, L.gridF);
+  if (L.gridS > 3 * nsm || L.gridF > 3 * nsm) return false;
   *out = L;
   return true;
 }
@@ -119,7 +131,7 @@ cudaError_t launch(const Problem& p, int mode, const Plan& L, const Bufs& B, con
     bgemm_kernel<<<L.gridB, NT, L.smemB, s>>>(T.b, p, B, L);
     n += 2;
   }
-  solve_kernel<<<L.gridS, SOLVE_T, 0, s>>>(p, B, L, mode);
+  solve_kernel<<<L.gridF, SOLVE_T, 0, s>>>(p, B, L, mode);
   ++n;
   if (mode != MODE_KKT) {
     pgemm_kernel<<<L.gridP, NT, L.smemP, s>>>(T.p, p, B, L);

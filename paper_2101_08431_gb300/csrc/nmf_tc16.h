@@ -24,8 +24,9 @@ struct Bufs {
   float* Bpart;               // [SB][mcap][16]: B partials, window column order
   unsigned char* Xs;          // split of X: ld/8 blocks of 512 bytes
   unsigned char* Ys;          // split of Y: one block of 512 bytes per 8 window columns
-  double* red;                // [gridS][16 * 16 + NYT] block partials of the solve kernel
-  unsigned* ticket;           // last-block ticket of the solve kernel (self-resetting)
+  double* red;                // [gridS][16 * 16 + NYT] block partials of the solve kernels, then their
+                              // group partials and the totals
+  unsigned* ticket;           // [ticket_count] tickets of the solve kernels' block sums (self-resetting)
   int* perm;                  // [mcap] window columns in the order of their passive sets
   int* perm_tmp;              // [mcap] the order after the first radix pass
   int* keys;                  // [mcap] passive-set mask of each window column
@@ -34,7 +35,8 @@ struct Bufs {
 struct Plan {
   int SB, SP;                 // row splits of the B-GEMM, column splits of the P-GEMM
   int gridB, gridP, gridS;
-  int cpg;                    // consecutive columns per 16-lane group of the solve kernel
+  int cpg;                    // consecutive columns per 16-lane group of the FP64 solve kernel (grid gridS)
+  int cpgF, gridF;            // the same for the FP32 solve kernel
   int NSB, NSP;               // stages of the two TMA rings
   size_t smemB, smemP;
 };
@@ -50,6 +52,7 @@ size_t bpart_bytes(int mcap);
 size_t xs_bytes(int ld);
 size_t ys_bytes(int mcap);
 size_t red_bytes(int nsm);
+size_t ticket_count(int nsm);   // unsigned counters behind Bufs::ticket
 // the three column-order arrays (perm, perm_tmp, keys), each of this size
 size_t perm_bytes(int mcap);
 // false when the driver entry point is missing or rejects the shape

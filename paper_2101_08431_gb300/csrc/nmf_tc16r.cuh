@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(TP) dfp_kernel(Problem p, RefPlan R, int mode)
 // row-block partials of dfb_kernel, and with record_refs B_ref = b,
 // Y_ref = the new y; kind INC: b = B_ref + the SB tensor-core partials of the
 // change, and the split of y - Y_ref for the incremental P-GEMM.  KKT terms
-// and H in FP64; the block partials are summed by the last block into
+// and H in FP64; the block partials are summed (tc16s::reduce_blocks) into
 // Hpart[0], Yterms[0] and entries 1 .. Q-1 are zeroed (Q: the P partials of
 // the pass).
 // ---------------------------------------------------------------------------
@@ -287,18 +287,10 @@ __global__ void __launch_bounds__(SOLVE_T, 2) solve64_kernel(Problem p, tc16s::B
     for (int w = 1; w < SOLVE_T / 32; ++w) v = (e == K * K + YT_YMAX) ? dmax_nn(v, wred[w][e]) : v + wred[w][e];
     myred[e] = v;
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) last = (atomicAdd(bf.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
+  const double* tot = tc16s::reduce_blocks(bf, &last);
+  if (!tot) return;
   for (int e = tid; e < RED; e += SOLVE_T) {
-    double v = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      const double w = bf.red[(size_t)b * RED + e];
-      v = (e == K * K + YT_YMAX) ? dmax_nn(v, w) : v + w;
-    }
+    const double v = tot[e];
     if (e < K * K) {
       p.Hpart[e] = (mode == MODE_KKT) ? 0.0 : v;
       for (int q = 1; q < Q; ++q) p.Hpart[(size_t)q * K * K + e] = 0.0;
@@ -307,7 +299,6 @@ __global__ void __launch_bounds__(SOLVE_T, 2) solve64_kernel(Problem p, tc16s::B
       for (int q = 1; q < Q; ++q) p.Yterms[(size_t)q * NYT + e - K * K] = 0.0;
     }
   }
-  if (tid == 0) *bf.ticket = 0u;
 }
 
 // split of X - X_ref for the incremental B-GEMM (rows >= n zero)

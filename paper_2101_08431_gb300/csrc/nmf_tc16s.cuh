@@ -72,6 +72,7 @@ constexpr int PG_ALO = PG_ROWS * PG_COLS * 2;
 
 constexpr int RED = K * K + NYT;   // per-block partials of the solve kernel: H, Y terms
 constexpr int SOLVE_T = 256;       // threads of the solve kernel (16 column groups)
+constexpr int RGROUP = 16;         // block partials summed per group before the groups are summed
 
 struct Ctl {
   uint64_t full[NSMAX];    // stage filled (tensor and bulk copies)
@@ -165,6 +166,73 @@ __device__ __forceinline__ void ctl_inval(Ctl& sm, int NS) {
 __device__ __forceinline__ void drain_fills(Ctl& sm, int NS, int issued) {
   for (int g = issued - NS; g < issued; ++g)
     if (g >= 0) timed_wait(&sm.full[g % NS], (uint32_t)((g / NS) & 1), WAIT_NS);
+}
+
+// Sum over the grid of the solve kernels' block partials (RED doubles per
+// block at red + block * RED, written by this block before the call), in a
+// fixed order whatever the order in which blocks finish: the last block of
+// each group of RGROUP consecutive blocks (ticket 1 + group) sums its group
+// in block order into a group partial, the last group to finish (ticket 0)
+// sums the group partials in group order.  Returns the totals (RED doubles)
+// in the one block that finishes, nullptr in every other block; each thread
+// of the finishing block owns the entries e = tid (mod blockDim.x) it wrote.
+// The tickets reset themselves.  Against one last block summing every block,
+// the tail on one SM is ~RGROUP + grid / RGROUP FP64 adds per entry instead
+// of grid adds (each FP64 warp instruction holds a sub-partition's unit for
+// tens of cycles on this part).
+__device__ __forceinline__ const double* reduce_blocks(const Bufs& bf, unsigned* s_last) {
+  const int tid = threadIdx.x, nb = (int)gridDim.x;
+  const int g = (int)blockIdx.x / RGROUP, ng = (nb + RGROUP - 1) / RGROUP;
+  const int b0 = g * RGROUP, b1 = min(nb, b0 + RGROUP);
+  double* grp = bf.red + (size_t)nb * RED;   // ng group partials, then the totals
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) *s_last = (atomicAdd(&bf.ticket[1 + g], 1u) == (unsigned)(b1 - b0 - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (!*s_last) return nullptr;
+  __threadfence();
+  for (int e = tid; e < RED; e += blockDim.x) {
+    double v = __ldcg(bf.red + (size_t)b0 * RED + e);
+    for (int b = b0 + 1; b < b1; ++b) {
+      const double w = __ldcg(bf.red + (size_t)b * RED + e);
+      v = (e == K * K + YT_YMAX) ? dmax_nn(v, w) : v + w;
+    }
+    grp[(size_t)g * RED + e] = v;
+  }
+  if (tid == 0) bf.ticket[1 + g] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) *s_last = (atomicAdd(&bf.ticket[0], 1u) == (unsigned)(ng - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (!*s_last) return nullptr;
+  __threadfence();
+  double* tot = grp + (size_t)ng * RED;
+  for (int e = tid; e < RED; e += blockDim.x) {
+    double v = __ldcg(grp + e);
+    for (int q = 1; q < ng; ++q) {
+      const double w = __ldcg(grp + (size_t)q * RED + e);
+      v = (e == K * K + YT_YMAX) ? dmax_nn(v, w) : v + w;
+    }
+    tot[e] = v;
+  }
+  if (tid == 0) bf.ticket[0] = 0u;
+  return tot;
+}
+
+// Knuth's two-sum: s + e == a + b exactly (round to nearest, no reassociation)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+// float-float accumulation (s, c) += (x, y): the rounding error of each FP32
+// add is carried in c, so sums of a few hundred terms keep FP64-class accuracy
+// with FP32 instructions only
+__device__ __forceinline__ void ff_add(float& s, float& c, float x, float y) {
+  float t, e;
+  two_sum(s, x, t, e);
+  s = t;
+  c += e + y;
 }
 
 // ---------------------------------------------------------------------------
@@ -674,14 +742,16 @@ __global__ void __launch_bounds__(SORT_T) sort_cols_kernel(Problem p, Bufs bf) {
 // BF16 split of the new y for the P-GEMM (zero for the padding columns of the
 // last 64-column granule).  This pass's b carries ~1e-5 relative error, so
 // its per-column arithmetic is FP32; the per-lane sums over a group's few
-// columns are FP32, everything summed across groups and blocks FP64.  The
-// block partials of H and the terms are summed by the last block (ticket) in
-// block order into Hpart[0], Yterms[0]; entries 1 .. Q-1 are written as zero,
-// so that the row pass's sum over Q partials (those of P) returns them.
+// columns are FP32, the sums across lanes and groups float-float (FP32
+// instructions carrying each add's rounding error), those across blocks FP64
+// (reduce_blocks, fixed order) into Hpart[0], Yterms[0]; entries 1 .. Q-1 are
+// written as zero, so that the row pass's sum over Q partials (those of P)
+// returns them.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, Plan L, int mode) {
   __shared__ float Gf[K][K + 1];
-  __shared__ double wred[SOLVE_T / 32][RED];
+  __shared__ float wfs[SOLVE_T / 16][RED];   // per 16-lane group: H entries and term sums
+  __shared__ float wfc[SOLVE_T / 16][NYT];   // the terms' float-float carries
   __shared__ unsigned last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   DevState* st = p.st;
@@ -696,7 +766,7 @@ __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, P
   const int a = nn.a;
   const int ncols = p.m, ncolp = (ncols + PG_COLS - 1) / PG_COLS * PG_COLS;
   const int gid = blockIdx.x * (SOLVE_T / 16) + (tid >> 4);
-  const int cbeg = min(ncolp, gid * L.cpg), cend = min(ncolp, cbeg + L.cpg);
+  const int cbeg = min(ncolp, gid * L.cpgF), cend = min(ncolp, cbeg + L.cpgF);
   float acc_t[NYT];
 #pragma unroll
   for (int e = 0; e < NYT; ++e) acc_t[e] = 0.f;
@@ -758,45 +828,47 @@ __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, P
       *reinterpret_cast<uint16_t*>(bf.Ys + xs_off(col, K + a)) = l;
     }
   }
-  // warp partials in FP64 (fixed order: the two halves, then the triangle entries)
-  double hd[9];
+  // group partials: H entries as the group's FP32 sums, the terms summed over
+  // the group's lanes as float-float pairs; then per block, each entry over
+  // the 16 groups in group order, float-float, to one double per entry
+  const int grp = tid >> 4;
 #pragma unroll
-  for (int d = 0; d < 9; ++d) hd[d] = (double)hacc[d] + (double)__shfl_xor_sync(0xffffffffu, hacc[d], 16);
-  if (lane < 16) {
-#pragma unroll
-    for (int d = 0; d < 9; ++d) {
-      const int c = (a + d) & 15;
-      if (d < 8 || a < 8) {
-        wred[warp][a * K + c] = hd[d];
-        wred[warp][c * K + a] = hd[d];
-      }
+  for (int d = 0; d < 9; ++d) {
+    const int c = (a + d) & 15;
+    if (d < 8 || a < 8) {
+      wfs[grp][a * K + c] = hacc[d];
+      wfs[grp][c * K + a] = hacc[d];
     }
   }
 #pragma unroll
   for (int e = 0; e < NYT; ++e) {
-    const double v = (e == YT_YMAX) ? warp_max((double)acc_t[e]) : warp_sum((double)acc_t[e]);
-    if (lane == 0) wred[warp][K * K + e] = v;
+    float sv = acc_t[e], cv = 0.f;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+      const float os = __shfl_xor_sync(nn.gm, sv, o), oc = __shfl_xor_sync(nn.gm, cv, o);
+      if (e == YT_YMAX) sv = fmaxf(sv, os);
+      else ff_add(sv, cv, os, oc);
+    }
+    if (a == 0) {
+      wfs[grp][K * K + e] = sv;
+      wfc[grp][e] = (e == YT_YMAX) ? 0.f : cv;
+    }
   }
   __syncthreads();
   double* myred = bf.red + (size_t)blockIdx.x * RED;
   for (int e = tid; e < RED; e += SOLVE_T) {
-    double v = wred[0][e];
-    for (int w = 1; w < SOLVE_T / 32; ++w) v = (e == K * K + YT_YMAX) ? dmax_nn(v, wred[w][e]) : v + wred[w][e];
-    myred[e] = v;
+    float sv = wfs[0][e], cv = e >= K * K ? wfc[0][e - K * K] : 0.f;
+    for (int g = 1; g < SOLVE_T / 16; ++g) {
+      if (e == K * K + YT_YMAX) sv = fmaxf(sv, wfs[g][e]);
+      else ff_add(sv, cv, wfs[g][e], e >= K * K ? wfc[g][e - K * K] : 0.f);
+    }
+    myred[e] = (double)sv + (double)cv;
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) last = (atomicAdd(bf.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
+  const double* tot = reduce_blocks(bf, &last);
+  if (!tot) return;
   const int Q = L.SP;
   for (int e = tid; e < RED; e += SOLVE_T) {
-    double v = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      const double w = bf.red[(size_t)b * RED + e];
-      v = (e == K * K + YT_YMAX) ? dmax_nn(v, w) : v + w;
-    }
+    const double v = tot[e];
     if (e < K * K) {
       p.Hpart[e] = (mode == MODE_KKT) ? 0.0 : v;
       for (int q = 1; q < Q; ++q) p.Hpart[(size_t)q * K * K + e] = 0.0;
@@ -805,7 +877,6 @@ __global__ void __launch_bounds__(SOLVE_T, 3) solve_kernel(Problem p, Bufs bf, P
       for (int q = 1; q < Q; ++q) p.Yterms[(size_t)q * NYT + e - K * K] = 0.0;
     }
   }
-  if (tid == 0) *bf.ticket = 0u;
 }
 
 }  // namespace tc16s

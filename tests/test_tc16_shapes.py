@@ -68,8 +68,16 @@ int main() {
           CHECK(L.gridB >= 1 && L.gridB <= 2 * nsm && L.gridP >= 1 && L.gridP <= 2 * nsm, "grids");
           CHECK(2 * (L.smemB + 1024) <= (size_t)optin + 1024 && 2 * (L.smemP + 1024) <= (size_t)optin + 1024,
                 "two CTAs per SM");
-          CHECK((size_t)L.gridS * RED * 8 <= red_bytes(nsm), "red");
+          {   // block partials, group partials and totals of reduce_blocks; its tickets
+            for (int grid : {L.gridS, L.gridF}) {
+              const size_t ngr = (grid + RGROUP - 1) / RGROUP;
+              CHECK(((size_t)grid + ngr + 1) * RED * 8 <= red_bytes(nsm), "red");
+              CHECK(1 + ngr <= ticket_count(nsm), "tickets");
+            }
+          }
           CHECK(L.cpg >= 1 && (long long)L.gridS * (SOLVE_T / 16) * L.cpg >= (long long)((m + PG_COLS - 1) / PG_COLS) * PG_COLS,
+                "solve groups cover the padded window");
+          CHECK(L.cpgF >= 1 && (long long)L.gridF * (SOLVE_T / 16) * L.cpgF >= (long long)((m + PG_COLS - 1) / PG_COLS) * PG_COLS,
                 "solve groups cover the padded window");
           // ---- B-GEMM
           const int ntile = (m + BG_COLS - 1) / BG_COLS;
