@@ -222,6 +222,7 @@ struct nmf_handle {
   double* dHpart = nullptr;
   double* dYterms = nullptr;
   double* dXpart = nullptr;
+  unsigned* dXgt = nullptr;      // k = 16: group tickets of the row pass
   DevState* dSt = nullptr;
   double* dKkt = nullptr;
   double* dSeed = nullptr;
@@ -374,6 +375,7 @@ Problem make_problem(const nmf_handle* h, int var) {
   p.Hpart = h->dHpart;
   p.Yterms = h->dYterms;
   p.Xpart = h->dXpart;
+  p.xgt = h->dXgt;
   p.st = h->dSt;
   p.Bref = h->dBref;
   p.Yref = h->dYref;
@@ -641,7 +643,7 @@ nmf_status nmf_destroy(nmf_handle* h) {
                    h->dHpart, h->dYterms, h->dXpart, h->dSt, h->dKkt, h->dSeed, h->dSeedMask,
                    h->dNonfinite, h->dStage, h->dBref, h->dYref, h->dPref, h->dXref, h->dXd32[0], h->dXd32[1],
                    h->dShard, h->dShardP, h->tcb.Bpart, h->tcb.Xs, h->tcb.Ys, h->tcb.red, h->tcb.ticket, h->tcb.perm, h->tcb.perm_tmp,
-                   h->tcb.keys, h->dBdf};
+                   h->tcb.keys, h->dBdf, h->dXgt};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (h->hSt) cudaFreeHost(h->hSt);
@@ -760,7 +762,9 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   ok &= cudaMalloc(&h->dPpart, (size_t)Qmax * h->ld * k * 8) == cudaSuccess;
   ok &= dalloc(&h->dHpart, (size_t)Qmax * k * k) == cudaSuccess;
   ok &= dalloc(&h->dYterms, (size_t)Qmax * NYT) == cudaSuccess;
-  ok &= dalloc(&h->dXpart, (size_t)h->nxblk * (k * k + NXT)) == cudaSuccess;
+  const int nxgrp = (h->nxblk + XGROUP - 1) / XGROUP;
+  ok &= dalloc(&h->dXpart, (size_t)(h->nxblk + (k == 16 ? nxgrp : 0)) * (k * k + NXT)) == cudaSuccess;
+  if (k == 16) ok &= cudaMalloc(&h->dXgt, (size_t)nxgrp * sizeof(unsigned)) == cudaSuccess;
   if (h->tc16) {
     ok &= cudaMalloc(&h->tcb.Bpart, tc16s::bpart_bytes(h->mcap)) == cudaSuccess;
     ok &= cudaMalloc(&h->tcb.Xs, tc16s::xs_bytes(h->ld)) == cudaSuccess;
@@ -783,6 +787,7 @@ nmf_status nmf_create(const nmf_config* cfg, nmf_handle** out) {
   if (!ok) return bail(NMF_ENOMEM, "device allocation failed");
   cudaMemsetAsync(h->dM, 0, (size_t)h->ld * (h->mcap + h->mirror) * (h->store_f32 ? 4 : 8), h->stream);
   cudaMemsetAsync(h->dSt, 0, sizeof(DevState), h->stream);
+  if (h->dXgt) cudaMemsetAsync(h->dXgt, 0, (size_t)nxgrp * sizeof(unsigned), h->stream);
   if (h->tc16) {
     cudaMemsetAsync(h->tcb.ticket, 0, tc16s::ticket_count(h->nsm) * sizeof(unsigned), h->stream);
     if (!tc16s::encode_maps(h->dM, h->ld, h->mcap, &h->tcmaps)) return bail(NMF_ECUDA, "tensor maps of M rejected");

@@ -93,7 +93,9 @@ struct Problem {
   void* Ppart;            // [Q][ld][k] partial M Y^T (accumulate type)
   double* Hpart;          // [Q][k][k]
   double* Yterms;         // [Q][NYT]
-  double* Xpart;          // [nxblk][k*k + NXT]
+  double* Xpart;          // [nxblk][k*k + NXT], for k = 16 then [ceil(nxblk / XGROUP)] group partials
+  unsigned* xgt;          // k = 16: group tickets of the row pass's block sums (self-resetting);
+                          // nullptr: the last block sums every block
   DevState* st;
   double kkt_target;      // <= 0 disables
   double kkt_abs_target;  // <= 0 disables
@@ -125,6 +127,8 @@ struct Problem {
 };
 
 enum Mode { MODE_SWEEP = 0, MODE_PRIME = 1, MODE_KKT = 2 };
+
+constexpr int XGROUP = 16;   // row-pass blocks per group partial (Problem::xgt)
 
 // ---------------------------------------------------------------------------
 // PTX wrappers

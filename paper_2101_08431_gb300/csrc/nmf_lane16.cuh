@@ -19,6 +19,11 @@ namespace nmfgb {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float vrcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double vrcp(double x) { return rcp64(x); }
+// bit patterns as signed integers: for values >= 0 (and -0) and negative
+// sentinels their order is that of the values, so maxima and arg-maxima of
+// such values take integer instructions instead of FP64 ones
+__device__ __forceinline__ int vbits(float x) { return __float_as_int(x); }
+__device__ __forceinline__ long long vbits(double x) { return __double_as_longlong(x); }
 
 template <typename V>
 struct LaneNnls16 {
@@ -55,9 +60,13 @@ struct LaneNnls16 {
     for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(gm, v, o);
     return v;
   }
+  // maximum over the group of values >= 0 (NaN only from non-finite input)
   __device__ __forceinline__ V gmaxv(V v) const {
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) v = fmax(v, __shfl_xor_sync(gm, v, o));
+    for (int o = 8; o >= 1; o >>= 1) {
+      const V w = __shfl_xor_sync(gm, v, o);
+      v = vbits(w) > vbits(v) ? w : v;
+    }
     return v;
   }
   __device__ __forceinline__ uint32_t gballot(bool p) const { return (__ballot_sync(gm, p) >> base) & 0xFFFFu; }
@@ -105,13 +114,13 @@ struct LaneNnls16 {
     const V tol = (V)(10.0 * K) * eps * (bmax + gmax * ymax);
     const V w = b - gdot(y);
     const bool cand = !(((P | blocked) >> a) & 1u) && w > tol;
-    V bw = cand ? w : (V)-1;
+    V bw = cand ? w : (V)-1;   // candidates: w > tol >= 0
     int bi = cand ? a : 99;
 #pragma unroll
     for (int o = 8; o >= 1; o >>= 1) {
       const V ow = __shfl_xor_sync(gm, bw, o);
       const int oi = __shfl_xor_sync(gm, bi, o);
-      if (ow > bw || (ow == bw && oi < bi)) {
+      if (vbits(ow) > vbits(bw) || (vbits(ow) == vbits(bw) && oi < bi)) {
         bw = ow;
         bi = oi;
       }

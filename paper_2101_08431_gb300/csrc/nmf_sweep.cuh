@@ -1281,11 +1281,39 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
   }
   // last block to finish: G for the next sweep, terms and statistics
   __syncthreads();
+  const double* xsrc = p.Xpart;
+  int nxsrc = nxblk;
+  if (K == 16 && p.xgt && !tail_done) {
+    // many blocks of 32 rows: the last block of each group of XGROUP sums its
+    // group in block order, and the last group's finisher the group partials
+    // in group order (one block summing every block's 272 values in FP64 took
+    // ~17 us at n = 8192)
+    const int g = blk / XGROUP, b0 = g * XGROUP, b1 = min(nxblk, b0 + XGROUP);
+    if (tid == 0) ticket = atomicAdd(&p.xgt[g], 1u);
+    __syncthreads();
+    if (ticket != (unsigned)(b1 - b0 - 1)) return;
+    __threadfence();
+    double* grp = p.Xpart + (size_t)nxblk * NV;
+    for (int e = tid; e < NV; e += T) {
+      const bool is_max = e == K * K + XT_XMAX;
+      double r = __ldcg(p.Xpart + (size_t)b0 * NV + e);
+      for (int b = b0 + 1; b < b1; ++b) {
+        const double w = __ldcg(p.Xpart + (size_t)b * NV + e);
+        r = is_max ? dmax_nn(r, w) : r + w;
+      }
+      grp[(size_t)g * NV + e] = r;
+    }
+    if (tid == 0) p.xgt[g] = 0u;
+    __threadfence();
+    __syncthreads();
+    xsrc = grp;
+    nxsrc = (nxblk + XGROUP - 1) / XGROUP;
+  }
   if (tid == 0) ticket = atomicAdd(&st->xblocks_done, 1u);
   __syncthreads();
-  if (ticket != (unsigned)(nxblk - 1)) return;
+  if (ticket != (unsigned)(nxsrc - 1)) return;
   __threadfence();
-  tree_sum2<T>(p.Xpart, nxblk, NV, NV, fin, K * K + XT_XMAX, p.Yterms, Q, NYT, NYT, yfin, YT_YMAX);
+  tree_sum2<T>(xsrc, nxsrc, NV, NV, fin, K * K + XT_XMAX, p.Yterms, Q, NYT, NYT, yfin, YT_YMAX);
   __syncthreads();
   if (tid < K * K) {
     p.G[tid] = fin[tid];
