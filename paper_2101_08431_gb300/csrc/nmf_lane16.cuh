@@ -24,6 +24,9 @@ __device__ __forceinline__ double vrcp(double x) { return rcp64(x); }
 // such values take integer instructions instead of FP64 ones
 __device__ __forceinline__ int vbits(float x) { return __float_as_int(x); }
 __device__ __forceinline__ long long vbits(double x) { return __double_as_longlong(x); }
+// x != 0 (either sign of zero) on the bit pattern
+__device__ __forceinline__ bool vnz(float x) { return ((unsigned)__float_as_int(x) << 1) != 0u; }
+__device__ __forceinline__ bool vnz(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull; }
 
 template <typename V>
 struct LaneNnls16 {
@@ -94,7 +97,7 @@ struct LaneNnls16 {
   }
   // (G y)_a
   __device__ V gdot(V y) const {
-    const uint32_t S = gballot(y != (V)0);
+    const uint32_t S = gballot(vnz(y));
     V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
@@ -148,9 +151,10 @@ struct LaneNnls16 {
 #pragma unroll
     for (int c = 0; c < K; ++c) {
       if ((P >> c) & 1u) {
+        // lane i: -u_c / s; the lanes of P: A_ac + u_a u_c / s (one FMA for both)
         const V uc = bc(u, c);
-        if (a == i) A[c] = -uc * rs;
-        else if (pa) A[c] = fmad(ua, uc, A[c]);
+        const V nv = fmad(a == i ? -rs : ua, uc, a == i ? (V)0 : A[c]);
+        if (a == i || pa) A[c] = nv;
       } else if (c == i) {
         if (a == i) A[c] = rs;
         else if (pa) A[c] = -ua;
@@ -336,14 +340,19 @@ struct LaneNnls16 {
 // (x, *mask set); otherwise x holds the refined point, a warm start for the
 // FP64 solve.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double resid64(const double* G64, double b, double x, unsigned gm, int base) {
+// (b - G x)_a over the components in S (x is zero outside S: the terms
+// skipped are exact zeros); S uniform on the group
+__device__ __forceinline__ double resid64(const double* G64, double b, double x, unsigned gm, int base, uint32_t S) {
   double s0 = b, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-  for (int c = 0; c < 16; c += 4) {
-    s0 = fmad(-G64[c], __shfl_sync(gm, x, base + c), s0);
-    s1 = fmad(-G64[c + 1], __shfl_sync(gm, x, base + c + 1), s1);
-    s2 = fmad(-G64[c + 2], __shfl_sync(gm, x, base + c + 2), s2);
-    s3 = fmad(-G64[c + 3], __shfl_sync(gm, x, base + c + 3), s3);
+  for (int c = 0; c < 16; ++c) {
+    if ((S >> c) & 1u) {
+      const double v = __shfl_sync(gm, x, base + c);
+      if ((c & 3) == 0) s0 = fmad(-G64[c], v, s0);
+      else if ((c & 3) == 1) s1 = fmad(-G64[c], v, s1);
+      else if ((c & 3) == 2) s2 = fmad(-G64[c], v, s2);
+      else s3 = fmad(-G64[c], v, s3);
+    }
   }
   return (s0 + s1) + (s2 + s3);
 }
@@ -358,21 +367,21 @@ __device__ __forceinline__ bool predict_refine16(LaneNnls16<float>& nf, const do
   *status = st;
   x = (double)xv;
   if (st != 0 || P != nf.Pc) return false;
-  double bmax = fabs(b);
+  double bmax = dabs(b);
 #pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(nf.gm, bmax, o));
+  for (int o = 8; o >= 1; o >>= 1) bmax = dmax_nn(bmax, __shfl_xor_sync(nf.gm, bmax, o));
   for (int round = 0; round < 3; ++round) {
     const bool inP = (P >> nf.a) & 1u;
     bool conv = false;
     for (int it = 0; it < maxit; ++it) {
-      const double rr = resid64(G64, b, x, nf.gm, nf.base);
+      const double rr = resid64(G64, b, x, nf.gm, nf.base, P);   // x is zero outside P
       const float dz = nf.apply(P, (float)rr);
       if (inP) x += (double)dz;
-      double dmax = inP ? fabs((double)dz) : 0.0, xmax = inP ? fabs(x) : 0.0;
+      double dmax = inP ? dabs((double)dz) : 0.0, xmax = inP ? dabs(x) : 0.0;
 #pragma unroll
       for (int o = 8; o >= 1; o >>= 1) {
-        dmax = fmax(dmax, __shfl_xor_sync(nf.gm, dmax, o));
-        xmax = fmax(xmax, __shfl_xor_sync(nf.gm, xmax, o));
+        dmax = dmax_nn(dmax, __shfl_xor_sync(nf.gm, dmax, o));
+        xmax = dmax_nn(xmax, __shfl_xor_sync(nf.gm, xmax, o));
       }
       if (dmax <= rtol * xmax) {
         conv = true;
@@ -381,10 +390,10 @@ __device__ __forceinline__ bool predict_refine16(LaneNnls16<float>& nf, const do
     }
     if (converge && !conv) return false;                // G_PP too ill conditioned for the FP32 inverse
     if (nf.gballot(inP && !(x > 0.0))) return false;   // infeasible: the FP64 solve decides
-    const double w = resid64(G64, b, x, nf.gm, nf.base);
-    double xmax = inP ? fabs(x) : 0.0;
+    const double w = resid64(G64, b, x, nf.gm, nf.base, P);
+    double xmax = inP ? dabs(x) : 0.0;
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(nf.gm, xmax, o));
+    for (int o = 8; o >= 1; o >>= 1) xmax = dmax_nn(xmax, __shfl_xor_sync(nf.gm, xmax, o));
     const double tol = 10.0 * K * eps * (bmax + gdiag_max * xmax);
     const bool cand = !inP && w > tol;
     if (!nf.gballot(cand)) {
@@ -400,7 +409,7 @@ __device__ __forceinline__ bool predict_refine16(LaneNnls16<float>& nf, const do
     for (int o = 8; o >= 1; o >>= 1) {
       const double ow = __shfl_xor_sync(nf.gm, bw, o);
       const int oi = __shfl_xor_sync(nf.gm, bi, o);
-      if (ow > bw || (ow == bw && oi < bi)) {
+      if (vbits(ow) > vbits(bw) || (vbits(ow) == vbits(bw) && oi < bi)) {   // candidates w > tol >= 0
         bw = ow;
         bi = oi;
       }

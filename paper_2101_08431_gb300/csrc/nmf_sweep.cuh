@@ -1216,17 +1216,26 @@ __device__ __forceinline__ void xpass_body(const Problem& p, int mode, int Q, in
     }
     // X-half KKT terms of the iterate leaving this sweep: graX = H x - P;
     // Gram partial: row a of x x^T
+    // components with x_c == 0 add exact zeros: skipped by branches uniform
+    // on the group (gx, the row's Gram terms) and on the warp (their sum over
+    // the two rows)
+    const uint32_t S = (__ballot_sync(ggm, vnz(xn)) >> gbase) & 0xFFFFu;
     double gx = -pr;
     double gr[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      const double xc = __shfl_sync(ggm, xn, gbase + c);
-      gx = fmad(H[a * K + c], xc, gx);
-      gr[c] = ract ? xn * xc : 0.0;
+      gr[c] = 0.0;
+      if ((S >> c) & 1u) {
+        const double xc = __shfl_sync(ggm, xn, gbase + c);
+        gx = fmad(H[a * K + c], xc, gx);
+        gr[c] = ract ? xn * xc : 0.0;
+      }
     }
     __syncwarp();
+    const uint32_t S2 = S | __shfl_xor_sync(0xffffffffu, S, 16);
 #pragma unroll
-    for (int c = 0; c < K; ++c) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], 16);
+    for (int c = 0; c < K; ++c)
+      if ((S2 >> c) & 1u) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], 16);
     if (lane < 16) {
 #pragma unroll
       for (int c = 0; c < K; ++c) gram_w[warp][c * K + a] = gr[c];   // G is symmetric: conflict-free order
