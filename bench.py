@@ -402,10 +402,19 @@ def run_ours(args):
     ms_f, _, tm_f = timed_sweeps(hf, nf, 3)
     yf = tm_f["ypass_ms"] / max(tm_f["ypass_launches"], 1)
     fbytes = N_ROWS * M_COLS * 8 + 2 * M_COLS * RANK_K * 8 + N_ROWS * RANK_K * 8
+    # the FP64 form's M pass against the measured FP64 FMA rate (4 n m k flops:
+    # the two contractions; an ALU roofline, the same kernel's HBM bytes beside)
+    from paper_2101_08431_gb300 import measure_fma_peaks
+    alu = measure_fma_peaks(sptr)
+    out["alu_peaks"] = dict(alu, how="independent FMA chains on every SM, CUDA events (nmf_measure_fma_peaks)")
+    f64_tfl = 4.0 * N_ROWS * M_COLS * RANK_K / (yf / 1e3) / 1e12
     out["pass_sweeps"]["fp64_form"] = {"sweeps_per_s": world * nf / (max_over_ranks(ms_f) / 1e3), "ypass_avg_ms": yf,
                                        "xpass_avg_ms": tm_f["xpass_ms"] / max(tm_f["xpass_launches"], 1),
                                        "ypass_gbs": fbytes / (yf / 1e3) / 1e9,
-                                       "ypass_fp64_tflops": 4.0 * N_ROWS * M_COLS * RANK_K / (yf / 1e3) / 1e12}
+                                       "ypass_fp64_tflops": f64_tfl,
+                                       "roofline": {"bound": "alu", "achieved": f64_tfl, "peak": alu["fp64_tflops"],
+                                                    "unit": "TFLOP/s", "frac": f64_tfl / alu["fp64_tflops"],
+                                                    "traffic": None, "peak_kind": "measured FP64 FMA rate"}}
     # ---- end to end through the C ABI with host buffers: every step copies M
     # (pinned), X0 and Y0 in, runs to the target, and copies X, Y and the
     # passive sets out

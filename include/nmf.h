@@ -448,6 +448,16 @@ nmf_status nmf_selftest_bounded_wait(int64_t polls, void *cuda_stream);
  * for a bad limit.  The paper has no counterpart. */
 nmf_status nmf_selftest_tc16_wait(int64_t limit_ms, void *cuda_stream);
 
+/* Measured FMA throughput of the current device, the denominators of the ALU
+ * rooflines (the FP64 form's M pass, the SIMT passes): out[0] = FP64, out[1]
+ * = FP32, in TFLOP/s (2 flops per FMA), each from one launch of independent
+ * FMA chains on every SM (after an untimed one) timed with CUDA events on
+ * cuda_stream (NULL: the legacy default stream).  out: 2 doubles of host
+ * memory, written on NMF_OK.  Allocates a 2 KB sink and two events and frees
+ * them.  Returns NMF_EINVAL for a NULL out, NMF_ECUDA on a CUDA error.  The
+ * paper has no counterpart. */
+nmf_status nmf_measure_fma_peaks(double *out, void *cuda_stream);
+
 /* Kernel launches issued by the batch (graph replays count their launches). */
 int64_t nmf_batch_launch_count(const nmf_batch *b);
 const char *nmf_batch_last_error(const nmf_batch *b);

@@ -16,7 +16,8 @@ from . import _native
 from ._native import (NMF_DTYPE_F32, NMF_DTYPE_F64, NMF_PREC_FP64, NMF_PREC_MIXED, NMF_WARM_COLD,
                       NMF_WARM_CHAIN, NMF_WARM_PREV, NMFError, check, load, nmf_config, nmf_stats)
 
-__all__ = ["StreamingNMF", "StreamingNMFBatch", "StreamingServer", "NMFError", "load", "nmf_config", "nmf_stats", "NMF_PREC_FP64",
+__all__ = ["StreamingNMF", "StreamingNMFBatch", "StreamingServer", "NMFError", "load", "nmf_config", "nmf_stats",
+           "measure_fma_peaks", "NMF_PREC_FP64",
            "NMF_PREC_MIXED", "NMF_DTYPE_F32", "NMF_DTYPE_F64", "NMF_WARM_COLD", "NMF_WARM_PREV", "NMF_WARM_CHAIN"]
 
 
@@ -402,3 +403,12 @@ class StreamingServer:
 
     def __exit__(self, *a):
         self.close()
+
+
+def measure_fma_peaks(stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s (2 flops per
+    FMA): {"fp64_tflops", "fp32_tflops"} (``nmf_measure_fma_peaks``)."""
+    lib = load()
+    out = (C.c_double * 2)()
+    check(lib.nmf_measure_fma_peaks(out, C.c_void_p(stream or 0)))
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1]}

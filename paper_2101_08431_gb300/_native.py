@@ -26,7 +26,7 @@ EXPORTS = ("nmf_config_init", "nmf_create", "nmf_destroy", "nmf_append_columns",
            "nmf_batch_create", "nmf_batch_destroy", "nmf_batch_size", "nmf_batch_problem",
            "nmf_batch_append_columns", "nmf_batch_set_factors", "nmf_batch_get_factors",
            "nmf_batch_set_pass_mode", "nmf_batch_set_schedule", "nmf_batch_sweep", "nmf_batch_autotune",
-           "nmf_batch_launch_count", "nmf_batch_last_error", "nmf_selftest_bounded_wait", "nmf_selftest_tc16_wait",
+           "nmf_batch_launch_count", "nmf_batch_last_error", "nmf_selftest_bounded_wait", "nmf_selftest_tc16_wait", "nmf_measure_fma_peaks",
            "nmf_server_config_init", "nmf_server_create", "nmf_server_destroy", "nmf_server_open_stream",
            "nmf_server_submit", "nmf_server_close_stream", "nmf_server_poll", "nmf_server_get_factors",
            "nmf_server_get_stats", "nmf_server_last_error")
@@ -158,6 +158,7 @@ def load(path: str = LIB_PATH):
     L.nmf_batch_last_error.restype = C.c_char_p
     L.nmf_selftest_bounded_wait.argtypes = [C.c_int64, C.c_void_p]
     L.nmf_selftest_tc16_wait.argtypes = [C.c_int64, C.c_void_p]
+    L.nmf_measure_fma_peaks.argtypes = [C.POINTER(C.c_double), C.c_void_p]
     S = C.c_void_p
     L.nmf_server_config_init.argtypes = [C.POINTER(nmf_server_config)]
     L.nmf_server_config_init.restype = None

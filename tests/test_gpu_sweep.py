@@ -405,3 +405,16 @@ def test_nonfinite_input_is_reported():
         h.append_columns(np.asfortranarray(cols))
     assert e.value.status == 7
     h.close()
+
+
+def test_measured_fma_peaks_are_plausible():
+    """nmf_measure_fma_peaks (the denominators of the ALU rooflines): FP64 and
+    FP32 FMA throughput of the device, positive and within an order of
+    magnitude of a Blackwell part's nominal rates (FP64 ~1.2 TFLOP/s on
+    GB300, FP32 SIMT ~80 TFLOP/s at the maximum clock)."""
+    _lib()
+    from paper_2101_08431_gb300 import measure_fma_peaks
+    pk = measure_fma_peaks()
+    assert 0.1 < pk["fp64_tflops"] < 100.0, pk
+    assert 8.0 < pk["fp32_tflops"] < 400.0, pk
+    assert pk["fp32_tflops"] > pk["fp64_tflops"], pk
