@@ -490,7 +490,7 @@ def run_ours(args):
                        "l2": "flushed (256 MB write) before every timed run; M (24 MB) stays in L2 within a run",
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU"}}
     for key in ("roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks", "time_to_kkt", "pass_sweeps",
-                "rank16", "batched", "chain_warm_start", "paper_shapes", "serving"):
+                "alu_peaks", "rank16", "batched", "chain_warm_start", "paper_shapes", "serving"):
         if key in out:
             line[key] = out[key]
     print(json.dumps(line), flush=True)
