@@ -220,7 +220,7 @@ __device__ __forceinline__ const double* reduce_blocks(const Bufs& bf, unsigned*
 }
 
 // Knuth's two-sum: s + e == a + b exactly (round to nearest, no reassociation)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bp = s - a;
   e = (a - (s - bp)) + (b - bp);
@@ -228,7 +228,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // float-float accumulation (s, c) += (x, y): the rounding error of each FP32
 // add is carried in c, so sums of a few hundred terms keep FP64-class accuracy
 // with FP32 instructions only
-__device__ __forceinline__ void ff_add(float& s, float& c, float x, float y) {
+__host__ __device__ __forceinline__ void ff_add(float& s, float& c, float x, float y) {
   float t, e;
   two_sum(s, x, t, e);
   s = t;
